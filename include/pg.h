@@ -1,0 +1,167 @@
+/*
+ * pg.h - C ABI of the GB300 parity-game solver (libpg.so).
+ *
+ * Greedy all-switches strategy improvement with best responses computed by
+ * one-player strategy improvement, after Fearnley, "Efficient Parallel
+ * Strategy Improvement for Parity Games" (arXiv 1705.02313).
+ *
+ * Conventions shared by every entry point:
+ *  - Games are CSR int32: offsets[n+1] (offsets[0] = 0, non-decreasing,
+ *    offsets[n] = m), targets[m] in [0, n), owner[n] (0 = Even, 1 = Odd),
+ *    pri[n] >= 0. Every vertex has at least one out-edge (Section 2: no
+ *    terminal vertices). This version requires pairwise distinct priorities,
+ *    the regime of the measured workloads (permuted priorities); a repeated
+ *    priority is rejected with PG_EUNSUPPORTED.
+ *  - mem_kind says where caller arrays live: PG_MEM_HOST (pageable or pinned
+ *    host memory) or PG_MEM_DEVICE (device memory of the context's GPU).
+ *    Caller arrays are read or written during the call only and never
+ *    retained. All work is ordered on the context's stream; every call
+ *    returns after its results are complete (host or device).
+ *  - Vertex ids in every input and output are the caller's original ids. The
+ *    admissibility preprocessing (Section 3, "The algorithm": dummy Even
+ *    vertices) adds k dummy vertices internally; they are reported only
+ *    through pg_game_info / pg_game_dummies and the dummy_sigma arrays.
+ *  - Every call returns a pg_status. No call aborts the process; on failure
+ *    pg_last_error() gives a message. Games are library-owned handles freed
+ *    with pg_game_free.
+ *
+ * Valuation encoding (Section 3, "Valuations"): with distinct priorities a
+ * finite valuation Val(v) is the set of vertices on the play from v to the
+ * sink, so the library reports, per vertex,
+ *   val_class  1 = TOP (infinite play), 0 = finite;
+ *   val_depth  number of vertices on the play before the sink (v and dummies
+ *              included), -1 for TOP;
+ *   val_rank   position of Val(v) in the total order of Section 3 among all
+ *              finite valuations of the game (dummies included) together with
+ *              the empty valuation of the sink, counted from 0; INT32_MAX for
+ *              TOP.
+ * Together with the strategies these determine every count vector exactly.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pg_status;
+
+#define PG_OK 0
+#define PG_EINVAL 1          /* malformed arguments or CSR */
+#define PG_ENOMEM 2          /* device or host allocation failed */
+#define PG_ETIMEOUT 3        /* iteration cap reached (Lemma 2 bounds the inner loop) */
+#define PG_ENOTADMISSIBLE 4  /* an odd cycle was met: sigma is not admissible (Section 3) */
+#define PG_ECUDA 5           /* a CUDA runtime error */
+#define PG_EUNSUPPORTED 6    /* input outside what this version handles */
+
+#define PG_MEM_HOST 0
+#define PG_MEM_DEVICE 1
+
+typedef struct pg_ctx pg_ctx;
+typedef struct pg_game pg_game;
+
+/* Solution of a game (Algorithm 1, Section 4). Every pointer is caller-owned
+ * and sized n (the original vertex count) unless stated; a NULL pointer skips
+ * that output. Theorem 1: W_Even is the set of TOP vertices under the final
+ * sigma. */
+typedef struct {
+    uint8_t *win;        /* 0 = Even wins, 1 = Odd wins (Section 2, winning sets) */
+    int32_t *sigma;      /* Even's final strategy; -1 = the sink, -1 for Odd vertices */
+    int32_t *tau;        /* Odd's best response to sigma; -1 for Even vertices */
+    int8_t *val_class;   /* see the valuation encoding above */
+    int32_t *val_depth;
+    int32_t *val_rank;
+    int8_t *dummy_sigma; /* k entries: 1 if dummy j moves on to its vertex, 0 if to the sink */
+    int32_t mem_kind;    /* where the arrays above live */
+    int64_t major;       /* out: outer iterations that switched Even's strategy */
+    int64_t inner;       /* out: valuations computed (total inner iterations) */
+} pg_result;
+
+/* Options of pg_solve; pass NULL for the defaults. */
+typedef struct {
+    const int32_t *sigma_init;     /* nullable warm start: Even strategy (-1 = sink), n entries */
+    const int32_t *tau_init;       /* nullable warm start: Odd strategy, n entries */
+    const int8_t *dummy_sigma_init;/* nullable: k entries, as in pg_result */
+    int32_t mem_kind;              /* where the warm-start arrays live */
+    int64_t max_inner;             /* cap on valuations computed; 0 = 64 * (n' + 64) */
+} pg_solve_opts;
+
+/* Valuation of one profile. Caller-owned arrays of n entries; NULL skips. */
+typedef struct {
+    int8_t *val_class;
+    int32_t *val_depth;
+    int32_t *val_rank;
+    int32_t *dom;        /* TOP vertices: largest priority on the cycle reached; -1 if finite */
+    int32_t mem_kind;
+} pg_valuation;
+
+/* Context: one GPU, one stream. device is the CUDA ordinal. */
+pg_status pg_ctx_create(pg_ctx **out, int device);
+void pg_ctx_destroy(pg_ctx *ctx);
+
+/* Orders all later work of ctx on stream (a cudaStream_t, e.g. a torch
+ * stream's handle); NULL selects the legacy default stream. */
+pg_status pg_set_stream(pg_ctx *ctx, void *stream);
+
+/* Message describing the last failure on ctx (never NULL). */
+const char *pg_last_error(const pg_ctx *ctx);
+
+/* Loads a game (Section 2) into library-owned device memory, validates it,
+ * and runs the admissibility preprocessing of Section 3 (dummy Even vertices
+ * in Odd's Even-free trap) and the internal relabelling. Returns PG_EINVAL
+ * for a malformed CSR (bad offsets, a vertex without edges, a target out of
+ * range, an owner other than 0/1, a negative priority, sizes beyond 2^30
+ * vertices or 2^31-1 edges after preprocessing) and PG_EUNSUPPORTED for
+ * repeated priorities. */
+pg_status pg_load_csr(pg_ctx *ctx, int32_t n, int64_t m, const int32_t *offsets, const int32_t *targets,
+                      const uint8_t *owner, const int32_t *pri, int32_t mem_kind, pg_game **out);
+
+/* Frees a game (NULL is ignored). */
+void pg_game_free(pg_game *game);
+
+/* Sizes of a loaded game: original n and m, dummies k (any pointer may be NULL). */
+pg_status pg_game_info(const pg_game *game, int32_t *n, int64_t *m, int32_t *k);
+
+/* The vertex each dummy guards: out[j] = w for dummy j (k entries, host memory). */
+pg_status pg_game_dummies(const pg_game *game, int32_t *out);
+
+/* Full solve: Algorithm 1 (Section 4) from sigma_init (every Even vertex to
+ * the sink, Section 3) and tau = the first edge of each list, or from the warm
+ * start in opts. Switching takes a successor only when strictly better and
+ * breaks ties by the lowest edge-list position, the sink first for Even.
+ * Returns PG_ETIMEOUT if the cap on valuations is reached (results then hold
+ * the last profile) and PG_ENOTADMISSIBLE if a warm start is not admissible. */
+pg_status pg_solve(pg_game *game, const pg_solve_opts *opts, pg_result *out);
+
+/* Best response to sigma (Section 4, one-player strategy improvement): the
+ * inner loop of Algorithm 1 only. sigma: n entries (-1 = sink; ignored for Odd
+ * vertices), dummy_sigma: k entries or NULL (all dummies to the sink, as in
+ * sigma_init), tau_inout: n entries or NULL; on entry the starting Odd
+ * strategy (NULL = first edges), on exit the best response. sigma must be
+ * admissible; an odd cycle met on the way returns PG_ENOTADMISSIBLE.
+ * iters_out (nullable, host) receives the number of valuations computed.
+ * All of sigma, dummy_sigma and tau_inout use mem_kind. */
+pg_status pg_best_response(pg_game *game, const int32_t *sigma, const int8_t *dummy_sigma, int32_t *tau_inout,
+                           int32_t mem_kind, pg_valuation *out, int64_t *iters_out);
+
+/* Valuation of any profile (Section 3; the pseudoforest of Section 5): class,
+ * depth and rank per vertex, and for TOP vertices the dominant priority of the
+ * cycle reached. An odd cycle is reported through dom (odd value) and the
+ * call returns PG_ENOTADMISSIBLE after filling the outputs. */
+pg_status pg_valuate(pg_game *game, const int32_t *sigma, const int8_t *dummy_sigma, const int32_t *tau,
+                     int32_t mem_kind, pg_valuation *out);
+
+/* Per-phase device time of the last pg_solve / pg_best_response / pg_valuate
+ * on game, in milliseconds, measured with CUDA events on the context's stream
+ * when timing is enabled (pg_set_timing). Each pointer may be NULL. */
+pg_status pg_set_timing(pg_ctx *ctx, int32_t enable);
+pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuation_ms, double *switch_ms,
+                         int64_t *valuations);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PG_H */

@@ -1,0 +1,442 @@
+// C ABI of libpg: contexts, games, and the loops of Algorithm 1 (Section 4).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+
+pg_status fail(pg_ctx* ctx, pg_status code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
+    if (ctx) ctx->err = m;
+    return e == cudaErrorMemoryAllocation ? PG_ENOMEM : PG_ECUDA;
+}
+
+void free_game(pg_game* g) {
+    if (!g) return;
+    void* ptrs[] = {g->off,  g->tgt,   g->flags, g->pri,   g->nid0,    g->orig_of, g->dnid, g->dummy_of,
+                    g->strat, g->gd,   g->plist, g->cls,   g->kind,    g->depth,   g->sz,   g->head,
+                    g->nxt,  g->wgt,   g->oddsz, g->key,   g->dom,     g->biglist, g->cnt,  g->scan_total,
+                    g->tile_e, g->tile_o, g->stage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& e : g->ev)
+        if (e) cudaEventDestroy(e);
+    delete g;
+}
+
+namespace {
+
+inline unsigned grid_of(int64_t n) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+// Sets g->strat from a profile given in original ids (NULL arrays take the
+// defaults: Even and dummies to the sink, Odd to its first edge).
+__global__ void k_apply_profile(int32_t n0, int32_t n, int32_t k, const int32_t* __restrict__ nid0,
+                                const int32_t* __restrict__ off, const int32_t* __restrict__ tgt,
+                                const uint8_t* __restrict__ flags, const int32_t* __restrict__ orig_of,
+                                const int32_t* __restrict__ dnid, const int32_t* sigma, const int32_t* tau,
+                                const int8_t* dsig, int32_t* strat, int32_t* err) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0 + (int64_t)k;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (v >= n0) {
+            int32_t d = dnid[v - n0];
+            strat[d] = (dsig && dsig[v - n0]) ? tgt[off[d]] : n;
+            continue;
+        }
+        int32_t i = nid0[v];
+        bool odd = (flags[i] & kOwnerOdd) != 0;
+        const int32_t* src = odd ? tau : sigma;
+        if (!src) {
+            strat[i] = odd ? tgt[off[i]] : n;
+            continue;
+        }
+        int32_t t = src[v];
+        if (!odd && t == -1) {
+            strat[i] = n;
+            continue;
+        }
+        int32_t pick = -1;
+        for (int32_t e = off[i]; e < off[i + 1]; ++e)
+            if (orig_of[tgt[e]] == t) {
+                pick = tgt[e];
+                break;
+            }
+        if (pick < 0) {
+            atomicOr(err, 1);
+            strat[i] = odd ? tgt[off[i]] : n;
+        } else {
+            strat[i] = pick;
+        }
+    }
+}
+
+struct OutPtrs {
+    uint8_t* win;
+    int32_t* sigma;
+    int32_t* tau;
+    int8_t* vclass;
+    int32_t* vdepth;
+    int32_t* vrank;
+    int32_t* vdom;
+    int8_t* dsig;
+};
+
+__global__ void k_results(int32_t n0, int32_t n, int32_t k, const int32_t* __restrict__ nid0,
+                          const int32_t* __restrict__ dnid, const uint8_t* __restrict__ flags,
+                          const int32_t* __restrict__ strat, const uint8_t* __restrict__ cls,
+                          const int32_t* __restrict__ depth, const int32_t* __restrict__ key,
+                          const int32_t* __restrict__ orig_of, const int32_t* __restrict__ dom, OutPtrs o) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0 + (int64_t)k;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (v >= n0) {
+            if (o.dsig) o.dsig[v - n0] = strat[dnid[v - n0]] != n;
+            continue;
+        }
+        int32_t i = nid0[v];
+        bool fin = cls[i] == kFin;
+        bool odd = (flags[i] & kOwnerOdd) != 0;
+        int32_t s = strat[i];
+        if (o.win) o.win[v] = fin ? 1 : 0;
+        if (o.sigma) o.sigma[v] = odd ? -1 : (s == n ? -1 : orig_of[s]);
+        if (o.tau) o.tau[v] = odd ? orig_of[s] : -1;
+        if (o.vclass) o.vclass[v] = fin ? 0 : 1;
+        if (o.vdepth) o.vdepth[v] = fin ? depth[i] : -1;
+        if (o.vrank) o.vrank[v] = fin ? key[i] : INT32_MAX;
+        if (o.vdom) o.vdom[v] = dom[i];
+    }
+}
+
+// staging layout for host outputs
+struct Stage {
+    size_t off_win, off_sigma, off_tau, off_class, off_depth, off_rank, off_dom, off_dsig, bytes;
+};
+inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+Stage stage_layout(int64_t n0, int64_t k) {
+    Stage s;
+    size_t p = 0;
+    s.off_win = p; p = al(p + n0);
+    s.off_sigma = p; p = al(p + 4 * n0);
+    s.off_tau = p; p = al(p + 4 * n0);
+    s.off_class = p; p = al(p + n0);
+    s.off_depth = p; p = al(p + 4 * n0);
+    s.off_rank = p; p = al(p + 4 * n0);
+    s.off_dom = p; p = al(p + 4 * n0);
+    s.off_dsig = p; p = al(p + k);
+    s.bytes = p;
+    return s;
+}
+
+pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
+                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    OutPtrs o = {win, sigma, tau, vclass, vdepth, vrank, vdom, dsig};
+    Stage L = stage_layout(g->n0, g->k);
+    if (mem_kind == PG_MEM_HOST) {
+        if (!g->stage) PG_CUDA_TRY(ctx, cudaMalloc(&g->stage, L.bytes));
+        char* b = (char*)g->stage;
+        o = {win ? (uint8_t*)(b + L.off_win) : nullptr,     sigma ? (int32_t*)(b + L.off_sigma) : nullptr,
+             tau ? (int32_t*)(b + L.off_tau) : nullptr,     vclass ? (int8_t*)(b + L.off_class) : nullptr,
+             vdepth ? (int32_t*)(b + L.off_depth) : nullptr, vrank ? (int32_t*)(b + L.off_rank) : nullptr,
+             vdom ? (int32_t*)(b + L.off_dom) : nullptr,     dsig ? (int8_t*)(b + L.off_dsig) : nullptr};
+    }
+    k_results<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->dnid, g->flags,
+                                                                g->strat, g->cls, g->depth, g->key, g->orig_of,
+                                                                g->dom, o);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    if (mem_kind == PG_MEM_HOST) {
+        size_t n0 = (size_t)g->n0;
+        auto cp = [&](void* dst, const void* src, size_t bytes) {
+            return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+        };
+        PG_CUDA_TRY(ctx, cp(win, o.win, n0));
+        PG_CUDA_TRY(ctx, cp(sigma, o.sigma, 4 * n0));
+        PG_CUDA_TRY(ctx, cp(tau, o.tau, 4 * n0));
+        PG_CUDA_TRY(ctx, cp(vclass, o.vclass, n0));
+        PG_CUDA_TRY(ctx, cp(vdepth, o.vdepth, 4 * n0));
+        PG_CUDA_TRY(ctx, cp(vrank, o.vrank, 4 * n0));
+        PG_CUDA_TRY(ctx, cp(vdom, o.vdom, 4 * n0));
+        PG_CUDA_TRY(ctx, cp(dsig, o.dsig, (size_t)g->k));
+    }
+    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return PG_OK;
+}
+
+// Copies caller profile arrays to the device when needed and applies them.
+pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, const int8_t* dsig, int32_t mem_kind) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    if (mem_kind != PG_MEM_HOST && mem_kind != PG_MEM_DEVICE) return fail(ctx, PG_EINVAL, "bad mem_kind");
+    const int32_t *ds = sigma, *dt = tau;
+    const int8_t* dd = dsig;
+    int32_t* buf = nullptr;
+    if (mem_kind == PG_MEM_HOST && (sigma || tau || dsig)) {
+        size_t bytes = 8 * (size_t)g->n0 + (size_t)g->k + 16;
+        PG_CUDA_TRY(ctx, cudaMalloc(&buf, bytes));
+        char* b = (char*)buf;
+        if (sigma) {
+            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b, sigma, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s));
+            ds = (const int32_t*)b;
+        }
+        if (tau) {
+            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b + 4 * (size_t)g->n0, tau, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s));
+            dt = (const int32_t*)(b + 4 * (size_t)g->n0);
+        }
+        if (dsig && g->k) {
+            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b + 8 * (size_t)g->n0, dsig, (size_t)g->k, cudaMemcpyHostToDevice, s));
+            dd = (const int8_t*)(b + 8 * (size_t)g->n0);
+        }
+    }
+    int32_t* err = &g->cnt->err;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        k_apply_profile<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->off, g->tgt,
+                                                                          g->flags, g->orig_of, g->dnid, ds, dt, dd,
+                                                                          g->strat, err);
+        e = cudaMemcpyAsync(ctx->pinned, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (buf) cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_profile");
+    if (ctx->pinned[0]) return fail(ctx, PG_EINVAL, "profile names a successor that is not an edge of its vertex");
+    return PG_OK;
+}
+
+struct Timer {
+    pg_game* g;
+    bool on;
+    explicit Timer(pg_game* gg) : g(gg), on(gg->ctx->timing) {
+        g->t_total = g->t_val = g->t_switch = 0;
+        g->t_vals = 0;
+    }
+    void mark(int i) {
+        if (on) cudaEventRecord(g->ev[i], g->ctx->stream);
+    }
+    double since(int a, int b) {
+        if (!on) return 0;
+        cudaEventSynchronize(g->ev[b]);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, g->ev[a], g->ev[b]);
+        return ms;
+    }
+};
+
+// The inner loop of Algorithm 1: valuations and Odd switches until no Odd
+// vertex switches. The last valuation is left in g (key, cls, depth).
+pg_status inner_loop(pg_game* g, int64_t cap, int64_t* inner, Timer& tm, bool* timed_out) {
+    *timed_out = false;
+    for (;;) {
+        if (*inner >= cap) {
+            *timed_out = true;
+            return PG_OK;
+        }
+        Counters hc;
+        tm.mark(0);
+        pg_status st = valuate_device(g, false, &hc);
+        if (st) return st;
+        tm.mark(1);
+        ++*inner;
+        if (hc.n_odd > 0)
+            return fail(g->ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
+        int32_t nsw = 0;
+        st = switch_device(g, 1, &nsw);
+        if (st) return st;
+        tm.mark(2);
+        g->t_val += tm.since(0, 1);
+        g->t_switch += tm.since(1, 2);
+        if (nsw == 0) return PG_OK;
+    }
+}
+
+}  // namespace
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" {
+
+pg_status pg_ctx_create(pg_ctx** out, int device) {
+    if (!out) return PG_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return PG_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return PG_ECUDA;
+    pg_ctx* c = new pg_ctx();
+    c->device = device;
+    if (cudaMallocHost((void**)&c->pinned, 64) != cudaSuccess) {
+        delete c;
+        return PG_ENOMEM;
+    }
+    *out = c;
+    return PG_OK;
+}
+
+void pg_ctx_destroy(pg_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+pg_status pg_set_stream(pg_ctx* ctx, void* stream) {
+    if (!ctx) return PG_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return PG_OK;
+}
+
+const char* pg_last_error(const pg_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+pg_status pg_set_timing(pg_ctx* ctx, int32_t enable) {
+    if (!ctx) return PG_EINVAL;
+    ctx->timing = enable != 0;
+    return PG_OK;
+}
+
+pg_status pg_last_timing(const pg_game* g, double* total_ms, double* valuation_ms, double* switch_ms,
+                         int64_t* valuations) {
+    if (!g) return PG_EINVAL;
+    if (total_ms) *total_ms = g->t_total;
+    if (valuation_ms) *valuation_ms = g->t_val;
+    if (switch_ms) *switch_ms = g->t_switch;
+    if (valuations) *valuations = g->t_vals;
+    return PG_OK;
+}
+
+pg_status pg_load_csr(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets,
+                      const uint8_t* owner, const int32_t* pri, int32_t mem_kind, pg_game** out) {
+    if (!ctx) return PG_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
+    return load_game(ctx, n, m, offsets, targets, owner, pri, mem_kind, out);
+}
+
+void pg_game_free(pg_game* game) { free_game(game); }
+
+pg_status pg_game_info(const pg_game* g, int32_t* n, int64_t* m, int32_t* k) {
+    if (!g) return PG_EINVAL;
+    if (n) *n = g->n0;
+    if (m) *m = g->m0;
+    if (k) *k = g->k;
+    return PG_OK;
+}
+
+pg_status pg_game_dummies(const pg_game* g, int32_t* out) {
+    if (!g || (!out && g->k)) return PG_EINVAL;
+    if (g->k == 0) return PG_OK;
+    cudaError_t e = cudaMemcpyAsync(out, g->dummy_of, sizeof(int32_t) * g->k, cudaMemcpyDeviceToHost, g->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->ctx->stream);
+    return e == cudaSuccess ? PG_OK : cuda_fail(g->ctx, e, "pg_game_dummies");
+}
+
+pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
+    if (!g || !out) return g ? fail(g->ctx, PG_EINVAL, "pg_solve: out is NULL") : PG_EINVAL;
+    pg_ctx* ctx = g->ctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
+    int64_t cap = (opts && opts->max_inner > 0) ? opts->max_inner : 64 * ((int64_t)g->n + 64);
+    pg_status st = apply_profile(g, opts ? opts->sigma_init : nullptr, opts ? opts->tau_init : nullptr,
+                                 opts ? opts->dummy_sigma_init : nullptr, opts ? opts->mem_kind : PG_MEM_HOST);
+    if (st) return st;
+    Timer tm(g);
+    tm.mark(3);
+    int64_t major = 0, inner = 0;
+    bool timed_out = false;
+    for (;;) {
+        st = inner_loop(g, cap, &inner, tm, &timed_out);
+        if (st) return st;
+        if (timed_out) break;
+        int32_t nsw = 0;
+        st = switch_device(g, 0, &nsw);
+        if (st) return st;
+        if (nsw == 0) break;
+        ++major;
+    }
+    if (timed_out) {
+        Counters hc;
+        st = valuate_device(g, false, &hc);  // valuation of the profile being returned
+        if (st) return st;
+    }
+    tm.mark(2);
+    g->t_total = tm.since(3, 2);
+    g->t_vals = inner;
+    out->major = major;
+    out->inner = inner;
+    st = write_outputs(g, out->mem_kind, out->win, out->sigma, out->tau, out->val_class, out->val_depth,
+                       out->val_rank, nullptr, out->dummy_sigma);
+    if (st) return st;
+    if (timed_out) return fail(ctx, PG_ETIMEOUT, "pg_solve: iteration cap reached");
+    return PG_OK;
+}
+
+pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma, int32_t* tau_inout,
+                           int32_t mem_kind, pg_valuation* out, int64_t* iters_out) {
+    if (!g) return PG_EINVAL;
+    pg_ctx* ctx = g->ctx;
+    if (!sigma) return fail(ctx, PG_EINVAL, "pg_best_response: sigma is NULL");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
+    pg_status st = apply_profile(g, sigma, tau_inout, dummy_sigma, mem_kind);
+    if (st) return st;
+    Timer tm(g);
+    tm.mark(3);
+    int64_t inner = 0;
+    bool timed_out = false;
+    st = inner_loop(g, 64 * ((int64_t)g->n + 64), &inner, tm, &timed_out);
+    if (iters_out) *iters_out = inner;
+    if (st) return st;
+    tm.mark(2);
+    g->t_total = tm.since(3, 2);
+    g->t_vals = inner;
+    st = write_outputs(g, mem_kind, nullptr, nullptr, tau_inout, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st) return st;
+    if (out) {
+        st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, out->val_class, out->val_depth,
+                           out->val_rank, nullptr, nullptr);
+        if (st) return st;
+        if (out->dom) {
+            // dom needs a valuation that records it
+            Counters hc;
+            st = valuate_device(g, true, &hc);
+            if (st) return st;
+            st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, out->dom,
+                               nullptr);
+            if (st) return st;
+        }
+    }
+    if (timed_out) return fail(ctx, PG_ETIMEOUT, "pg_best_response: iteration cap reached");
+    return PG_OK;
+}
+
+pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma, const int32_t* tau,
+                     int32_t mem_kind, pg_valuation* out) {
+    if (!g) return PG_EINVAL;
+    pg_ctx* ctx = g->ctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
+    pg_status st = apply_profile(g, sigma, tau, dummy_sigma, mem_kind);
+    if (st) return st;
+    Timer tm(g);
+    tm.mark(0);
+    Counters hc;
+    st = valuate_device(g, true, &hc);
+    if (st) return st;
+    tm.mark(1);
+    g->t_val = g->t_total = tm.since(0, 1);
+    g->t_vals = 1;
+    if (out) {
+        st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, out->val_class, out->val_depth, out->val_rank,
+                           out->dom, nullptr);
+        if (st) return st;
+    }
+    if (hc.n_odd > 0) return fail(ctx, PG_ENOTADMISSIBLE, "pg_valuate: the profile reaches an odd cycle");
+    return PG_OK;
+}
+
+}  // extern "C"

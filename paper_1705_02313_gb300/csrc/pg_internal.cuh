@@ -1,0 +1,159 @@
+// Internal declarations of libpg (GB300, sm_103a).
+//
+// Device layout of a loaded game. After the admissibility preprocessing
+// (Section 3) the game G' has n vertices; they are relabelled so that a
+// vertex id is the rank of its priority among all n priorities (priorities
+// are pairwise distinct). "Higher priority" is then "larger id", the parity
+// of the priority is kept in a flag bit, and the sink is the id n, above
+// every vertex, which is what the nearest-greater-ancestor walks need.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/pg.h"
+
+namespace pg {
+
+constexpr int kBlock = 256;
+constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
+constexpr int kSmallChildren = 32;    // children handled by one thread in the per-parent pass
+constexpr int kBlockChildren = 4096;  // children handled by one block (shared-memory sort)
+
+// flags[v]
+constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
+constexpr uint8_t kPriOdd = 2;     // priority is odd
+
+// cls[v]
+constexpr uint8_t kFin = 0;
+constexpr uint8_t kTop = 1;
+constexpr uint8_t kOddCycle = 2;
+
+// Packed nearest-greater-ancestor word gd[v]:
+//   bits 0..31  ptr  (a vertex id, the sink id n, or for "none" vertices the id of the cycle maximum)
+//   bits 32..61 dist (number of steps from v to ptr along the successor function)
+//   bit  62     none (v is above every vertex of its infinite future)
+//   bit  63     resolved (ptr is final; otherwise ptr is a jump pointer: every vertex strictly between v and ptr is below v)
+constexpr uint64_t kResolved = 1ull << 63;
+constexpr uint64_t kNone = 1ull << 62;
+__host__ __device__ inline uint64_t gd_pack(bool resolved, bool none, uint32_t dist, int32_t ptr) {
+    return (resolved ? kResolved : 0ull) | (none ? kNone : 0ull) | ((uint64_t)(dist & 0x3fffffffu) << 32) |
+           (uint64_t)(uint32_t)ptr;
+}
+__host__ __device__ inline int32_t gd_ptr(uint64_t w) { return (int32_t)(uint32_t)(w & 0xffffffffull); }
+__host__ __device__ inline uint32_t gd_dist(uint64_t w) { return (uint32_t)((w >> 32) & 0x3fffffffu); }
+__host__ __device__ inline bool gd_resolved(uint64_t w) { return (w & kResolved) != 0; }
+__host__ __device__ inline bool gd_none(uint64_t w) { return (w & kNone) != 0; }
+
+// kind[v] written by the first chain pass
+constexpr uint8_t kKindFin = 1;        // finite valuation
+constexpr uint8_t kKindSinkChild = 2;  // nearest greater ancestor is the sink
+
+// Device counters of one game (one cache line each would be overkill; a small struct in device memory).
+struct Counters {
+    int32_t n_pending;   // vertices left to the pointer-jumping phase
+    int32_t n_fin;       // finite vertices
+    int32_t n_odd;       // vertices reaching an odd cycle
+    int32_t n_big;       // parents with more than kSmallChildren children
+    int32_t n_switch;    // switched vertices in the last switching pass
+    int32_t err;         // device-side error bits
+    int32_t sink_rank;   // rank of the sink's empty valuation
+    int32_t pad;
+};
+constexpr int32_t kErrTooManyChildren = 1;
+constexpr int32_t kErrJumpRounds = 2;
+
+struct Game;
+
+// scan helpers (pg_scan.cu)
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total; int64 accumulation, int32 output.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total_dev, void* tmp,
+                               size_t tmp_bytes, cudaStream_t s);
+size_t scan_tmp_bytes(int64_t n);
+// Exclusive scan of 0/1 bytes.
+cudaError_t exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                              cudaStream_t s);
+// Exclusive popcount scan over 32-bit words: out[i] = popcount of words[0..i).
+cudaError_t exclusive_popc_scan(const uint32_t* words, int32_t* out, int64_t nwords, void* tmp,
+                                size_t tmp_bytes, cudaStream_t s);
+
+}  // namespace pg
+
+// Library objects
+struct pg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+    bool timing = false;
+    int32_t* pinned = nullptr;  // small pinned host buffer for counters
+};
+
+struct pg_game {
+    pg_ctx* ctx = nullptr;
+    int32_t n0 = 0;   // original vertex count
+    int64_t m0 = 0;   // original edge count
+    int32_t k = 0;    // dummies
+    int32_t n = 0;    // n' = n0 + k
+    int64_t m = 0;    // m' = m0 + k
+    // relabelled G'
+    int32_t* off = nullptr;      // [n+1]
+    int32_t* tgt = nullptr;      // [m]
+    uint8_t* flags = nullptr;    // [n]
+    int32_t* pri = nullptr;      // [n] priority in G'
+    int32_t* nid0 = nullptr;     // [n0] original vertex -> relabelled id
+    int32_t* orig_of = nullptr;  // [n] relabelled id -> original vertex (a dummy reports the vertex it guards)
+    int32_t* dnid = nullptr;     // [k] dummy j -> relabelled id
+    int32_t* dummy_of = nullptr; // [k] dummy j -> original vertex it guards (device)
+    // solver state
+    int32_t* strat = nullptr;    // [n] successor under the current profile; n = the sink
+    // per-iteration scratch
+    uint64_t* gd = nullptr;      // [n] nearest-greater words
+    int32_t* plist = nullptr;    // [n] pending list
+    uint8_t* cls = nullptr;      // [n]
+    uint8_t* kind = nullptr;     // [n]
+    int32_t* depth = nullptr;    // [n]
+    int32_t* sz = nullptr;       // [n] proper descendants in the nearest-greater forest
+    int32_t* head = nullptr;     // [n] first child (non-sink parents), -1 none
+    int32_t* nxt = nullptr;      // [n] next sibling
+    int32_t* wgt = nullptr;      // [n] chain weight: [even] + sizes of siblings ordered before
+    int32_t* oddsz = nullptr;    // [n] sizes of odd children
+    int32_t* key = nullptr;      // [n+1] rank; INT32_MAX for TOP; key[n] = sink rank
+    int32_t* dom = nullptr;      // [n] dominant priority of the cycle reached (TOP), -1 finite
+    int32_t* biglist = nullptr;  // [n] parents with many children
+    pg::Counters* cnt = nullptr; // device counters
+    void* scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    int64_t* scan_total = nullptr;
+    int32_t* tile_e = nullptr;   // sink-scan tile sums (even)
+    int32_t* tile_o = nullptr;   // sink-scan tile sums (odd)
+    int64_t ntiles = 0;
+    void* stage = nullptr;       // staging for host outputs
+    // timing of the last call
+    double t_total = 0, t_val = 0, t_switch = 0;
+    int64_t t_vals = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// internal entry points shared by the translation units
+namespace pg {
+pg_status fail(pg_ctx* ctx, pg_status code, const std::string& msg);
+pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where);
+pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const int32_t* tgt,
+                    const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out);
+pg_status alloc_scratch(pg_game* g);
+void free_game(pg_game* g);
+// one valuation of g->strat: fills cls, depth, key (and dom when want_dom). Returns counters on host.
+pg_status valuate_device(pg_game* g, bool want_dom, Counters* host_cnt);
+// one switching pass for player (0 Even, 1 Odd) using g->key; returns switched count.
+pg_status switch_device(pg_game* g, int player, int32_t* nswitch);
+}  // namespace pg
+
+#define PG_CUDA_TRY(ctx, expr)                                    \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return pg::cuda_fail((ctx), _e, #expr); \
+    } while (0)

@@ -1,0 +1,362 @@
+// Loading a game: validation, the admissibility preprocessing of Section 3
+// ("The algorithm": dummy Even vertices in Odd's Even-free trap), and the
+// relabelling of G' by priority rank. Runs once per game, entirely on the
+// device; only a few scalars cross to the host (sizes and error bits).
+#include <stdio.h>
+
+#include <vector>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+constexpr int32_t kEOff = 1, kETgt = 2, kEOwn = 4, kEPri = 8, kEDup = 16;
+
+struct LoadScalars {
+    int32_t err;
+    int32_t maxpri;
+    int32_t frontier;
+    int32_t pad;
+};
+
+inline unsigned nblocks(int64_t n, int per = kBlock) {
+    int64_t b = (n + per - 1) / per;
+    if (b < 1) b = 1;
+    if (b > (1ll << 30)) b = 1ll << 30;
+    return (unsigned)b;
+}
+
+__global__ void k_validate(int32_t n, int64_t m, const int32_t* off, const int32_t* tgt, const uint8_t* own,
+                           const int32_t* pri, LoadScalars* sc) {
+    int32_t err = 0, mx = -1;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = off[v], b = off[v + 1];
+        if (b <= a || a < 0 || (int64_t)b > m) err |= kEOff;
+        if (v == 0 && a != 0) err |= kEOff;
+        if (v == n - 1 && (int64_t)b != m) err |= kEOff;
+        if (own[v] > 1) err |= kEOwn;
+        if (pri[v] < 0) err |= kEPri;
+        if (pri[v] > mx) mx = pri[v];
+        if (!(err & kEOff))
+            for (int32_t e = a; e < b; ++e)
+                if (tgt[e] < 0 || tgt[e] >= n) err |= kETgt;
+    }
+    if (err) atomicOr(&sc->err, err);
+    atomicMax(&sc->maxpri, mx);
+}
+
+// Marks every priority in a bitmap; a bit already set means a repeated priority.
+__global__ void k_mark_priorities(int32_t n, const int32_t* pri, int32_t shift_orig, int32_t n_orig,
+                                  uint32_t* bits, LoadScalars* sc) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        // vertices below n_orig are original (priority shifted by shift_orig); the rest are dummies with 2j
+        int64_t p = v < n_orig ? (int64_t)pri[v] + shift_orig : 2 * (v - n_orig);
+        uint32_t bit = 1u << (p & 31);
+        uint32_t old = atomicOr(&bits[p >> 5], bit);
+        if (old & bit) atomicOr(&sc->err, kEDup);
+    }
+}
+
+__global__ void k_indegree(int64_t m, const int32_t* tgt, int32_t* indeg) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&indeg[tgt[e]], 1);
+}
+
+__global__ void k_reverse_scatter(int32_t n, const int32_t* off, const int32_t* tgt, int32_t* fill, int32_t* radj) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) radj[atomicAdd(&fill[tgt[e]], 1)] = (int32_t)v;
+}
+
+// U starts as every Odd vertex; cnt[v] = edges of v into Odd vertices. Odd
+// vertices without such an edge leave U first.
+__global__ void k_trap_init(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* own, uint8_t* inU,
+                            int32_t* cnt, int32_t* frontier, LoadScalars* sc) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (own[v] != 1) {
+            inU[v] = 0;
+            continue;
+        }
+        int32_t c = 0;
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) c += own[tgt[e]] == 1;
+        cnt[v] = c;
+        inU[v] = c > 0;
+        if (c == 0) frontier[atomicAdd(&sc->frontier, 1)] = (int32_t)v;
+    }
+}
+
+// Peeling round: every vertex x that just left U decrements the count of its
+// Odd predecessors; a predecessor whose count reaches zero leaves U next.
+__global__ void k_trap_peel(int32_t nf, const int32_t* frontier, const int32_t* roff, const int32_t* radj,
+                            const uint8_t* own, uint8_t* inU, int32_t* cnt, int32_t* next, LoadScalars* sc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = frontier[i];
+        for (int32_t r = roff[x]; r < roff[x + 1]; ++r) {
+            int32_t y = radj[r];
+            if (own[y] == 1 && atomicSub(&cnt[y], 1) == 1) {
+                inU[y] = 0;
+                next[atomicAdd(&sc->frontier, 1)] = y;
+            }
+        }
+    }
+}
+
+// W: vertices of U entered by an edge from U.
+__global__ void k_mark_w(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* inU, uint8_t* isW) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (!inU[v]) continue;
+        for (int32_t e = off[v]; e < off[v + 1]; ++e)
+            if (inU[tgt[e]]) isW[tgt[e]] = 1;
+    }
+}
+
+__global__ void k_dummy_of(int32_t n, const uint8_t* isW, const int32_t* widx, int32_t* dummy_of) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x)
+        if (isW[w]) dummy_of[widx[w]] = (int32_t)w;
+}
+
+__device__ inline int32_t prio_of(int64_t v, int32_t n0, const int32_t* pri, int32_t k) {
+    return v < n0 ? pri[v] + 2 * k : (int32_t)(2 * (v - n0));
+}
+
+// relabelled id of every G' vertex = rank of its priority
+__global__ void k_rank(int32_t np, int32_t n0, int32_t k, const int32_t* pri, const uint32_t* bits,
+                       const int32_t* wprefix, int32_t* nid, int32_t* gid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < np; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p = prio_of(v, n0, pri, k);
+        int32_t r = wprefix[p >> 5] + __popc(bits[p >> 5] & ((1u << (p & 31)) - 1u));
+        nid[v] = r;
+        gid[r] = (int32_t)v;
+    }
+}
+
+__global__ void k_relabel_degree(int32_t np, int32_t n0, const int32_t* off, const int32_t* gid, int32_t* deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t src = gid[i];
+        deg[i] = src < n0 ? off[src + 1] - off[src] : 1;
+    }
+}
+
+__global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int32_t* off, const int32_t* tgt,
+                               const uint8_t* own, const int32_t* pri, const uint8_t* inU, const int32_t* widx,
+                               const int32_t* dummy_of, const int32_t* gid, const int32_t* nid,
+                               const int32_t* roff, int32_t* rtgt, uint8_t* rflags, int32_t* rpri,
+                               int32_t* orig_of) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t src = gid[i];
+        int32_t p = prio_of(src, n0, pri, k);
+        int32_t base = roff[i];
+        if (src < n0) {
+            bool u = inU[src] != 0;
+            for (int32_t e = off[src]; e < off[src + 1]; ++e) {
+                int32_t t = tgt[e];
+                int32_t tp = (u && inU[t]) ? n0 + widx[t] : t;  // redirect U -> W edges to the dummy
+                rtgt[base + (e - off[src])] = nid[tp];
+            }
+            rflags[i] = (uint8_t)((own[src] ? kOwnerOdd : 0) | ((p & 1) ? kPriOdd : 0));
+            orig_of[i] = src;
+        } else {
+            int32_t w = dummy_of[src - n0];
+            rtgt[base] = nid[w];
+            rflags[i] = (uint8_t)((p & 1) ? kPriOdd : 0);  // dummies are Even
+            orig_of[i] = w;
+        }
+        rpri[i] = p;
+    }
+}
+
+__global__ void k_maps(int32_t n0, int32_t k, const int32_t* nid, int32_t* nid0, int32_t* dnid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0 + (int64_t)k;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (v < n0) nid0[v] = nid[v];
+        else dnid[v - n0] = nid[v];
+    }
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count) {
+    return cudaMalloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T));
+}
+
+struct Temps {
+    std::vector<void*> ptrs;
+    ~Temps() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t get(T** p, int64_t count) {
+        cudaError_t e = dalloc(p, count);
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        return e;
+    }
+};
+
+}  // namespace
+
+pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, const int32_t* tgt_in,
+                    const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out) {
+    if (!out) return fail(ctx, PG_EINVAL, "pg_load_csr: out is NULL");
+    *out = nullptr;
+    if (!off_in || !tgt_in || !own_in || !pri_in) return fail(ctx, PG_EINVAL, "pg_load_csr: NULL array");
+    if (mem_kind != PG_MEM_HOST && mem_kind != PG_MEM_DEVICE) return fail(ctx, PG_EINVAL, "pg_load_csr: bad mem_kind");
+    if (n < 1 || n >= (1 << 30)) return fail(ctx, PG_EINVAL, "pg_load_csr: n must be in [1, 2^30)");
+    if (m < n || m > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: m must be in [n, 2^31-1)");
+    cudaStream_t s = ctx->stream;
+    cudaMemcpyKind kind = mem_kind == PG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    Temps T;
+    int32_t *off, *tgt, *pri;
+    uint8_t* own;
+    LoadScalars* sc;
+    PG_CUDA_TRY(ctx, T.get(&off, (int64_t)n + 1));
+    PG_CUDA_TRY(ctx, T.get(&tgt, m));
+    PG_CUDA_TRY(ctx, T.get(&own, n));
+    PG_CUDA_TRY(ctx, T.get(&pri, n));
+    PG_CUDA_TRY(ctx, T.get(&sc, 1));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(off, off_in, sizeof(int32_t) * ((size_t)n + 1), kind, s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(tgt, tgt_in, sizeof(int32_t) * (size_t)m, kind, s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(own, own_in, (size_t)n, kind, s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(pri, pri_in, sizeof(int32_t) * (size_t)n, kind, s));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(sc, 0, sizeof(LoadScalars), s));
+    {
+        LoadScalars init = {0, -1, 0, 0};
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    }
+    k_validate<<<nblocks(n), kBlock, 0, s>>>(n, m, off, tgt, own, pri, sc);
+    LoadScalars h;
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h.err & kEOff) return fail(ctx, PG_EINVAL, "pg_load_csr: offsets must start at 0, end at m, and give every vertex at least one edge");
+    if (h.err & kETgt) return fail(ctx, PG_EINVAL, "pg_load_csr: edge target out of range");
+    if (h.err & kEOwn) return fail(ctx, PG_EINVAL, "pg_load_csr: owner must be 0 (Even) or 1 (Odd)");
+    if (h.err & kEPri) return fail(ctx, PG_EINVAL, "pg_load_csr: negative priority");
+    int32_t maxpri = h.maxpri;
+
+    // repeated priorities are outside this version
+    {
+        int64_t nwords = ((int64_t)maxpri >> 5) + 1;
+        uint32_t* bits;
+        PG_CUDA_TRY(ctx, T.get(&bits, nwords));
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)nwords, s));
+        k_mark_priorities<<<nblocks(n), kBlock, 0, s>>>(n, pri, 0, n, bits, sc);
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (h.err & kEDup)
+            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities are not supported by this version");
+    }
+
+    // reverse adjacency for the trap computation
+    int32_t *indeg, *roff, *radj, *fill, *cnt, *fa, *fb, *widx;
+    uint8_t *inU, *isW;
+    size_t stb = scan_tmp_bytes((int64_t)n + 2) + 64;
+    void* stmp;
+    PG_CUDA_TRY(ctx, T.get((char**)&stmp, (int64_t)stb));
+    PG_CUDA_TRY(ctx, T.get(&indeg, n));
+    PG_CUDA_TRY(ctx, T.get(&roff, (int64_t)n + 1));
+    PG_CUDA_TRY(ctx, T.get(&radj, m));
+    PG_CUDA_TRY(ctx, T.get(&fill, (int64_t)n + 1));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (size_t)n, s));
+    k_indegree<<<nblocks(m), kBlock, 0, s>>>(m, tgt, indeg);
+    PG_CUDA_TRY(ctx, exclusive_scan_i32(indeg, roff, n, nullptr, stmp, stb, s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(fill, roff, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+    k_reverse_scatter<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, fill, radj);
+
+    // U: greatest fixpoint by peeling
+    PG_CUDA_TRY(ctx, T.get(&cnt, n));
+    PG_CUDA_TRY(ctx, T.get(&fa, n));
+    PG_CUDA_TRY(ctx, T.get(&fb, n));
+    PG_CUDA_TRY(ctx, T.get(&inU, n));
+    k_trap_init<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, inU, cnt, fa, sc);
+    for (int64_t round = 0;; ++round) {
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        int32_t nf = h.frontier;
+        if (nf == 0) break;
+        if (round > n) return fail(ctx, PG_EINVAL, "pg_load_csr: trap peeling did not converge");
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(&sc->frontier, 0, sizeof(int32_t), s));
+        k_trap_peel<<<nblocks(nf), kBlock, 0, s>>>(nf, fa, roff, radj, own, inU, cnt, fb, sc);
+        int32_t* t = fa;
+        fa = fb;
+        fb = t;
+    }
+    PG_CUDA_TRY(ctx, T.get(&isW, n));
+    PG_CUDA_TRY(ctx, T.get(&widx, (int64_t)n + 1));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(isW, 0, (size_t)n, s));
+    k_mark_w<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, inU, isW);
+    PG_CUDA_TRY(ctx, exclusive_scan_u8(isW, widx, n, stmp, stb, s));
+    int32_t k = 0;
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(&k, widx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t np = (int64_t)n + k, mp = m + k;
+    if (np >= (1 << 30)) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^30 vertices after preprocessing");
+    if (mp > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^31-2 edges after preprocessing");
+    if ((int64_t)maxpri + 2 * (int64_t)k > INT32_MAX - 1)
+        return fail(ctx, PG_EINVAL, "pg_load_csr: priorities too large for the preprocessing shift");
+
+    pg_game* g = new pg_game();
+    g->ctx = ctx;
+    g->n0 = n;
+    g->m0 = m;
+    g->k = k;
+    g->n = (int32_t)np;
+    g->m = mp;
+    auto bail = [&](cudaError_t e, const char* where) {
+        free_game(g);
+        return cuda_fail(ctx, e, where);
+    };
+#define LG_TRY(expr)                                  \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return bail(_e, #expr); \
+    } while (0)
+    LG_TRY(dalloc(&g->off, np + 1));
+    LG_TRY(dalloc(&g->tgt, mp));
+    LG_TRY(dalloc(&g->flags, np));
+    LG_TRY(dalloc(&g->pri, np));
+    LG_TRY(dalloc(&g->nid0, n));
+    LG_TRY(dalloc(&g->orig_of, np));
+    LG_TRY(dalloc(&g->dnid, k));
+    LG_TRY(dalloc(&g->dummy_of, k));
+    LG_TRY(dalloc(&g->strat, np));
+    k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
+
+    // ranks of the G' priorities
+    int64_t pmax = (int64_t)maxpri + 2 * (int64_t)k;
+    int64_t nw = (pmax >> 5) + 1;
+    uint32_t* bits2;
+    int32_t *wprefix, *nid, *gid, *deg;
+    LG_TRY(T.get(&bits2, nw));
+    LG_TRY(T.get(&wprefix, nw + 1));
+    LG_TRY(T.get(&nid, np));
+    LG_TRY(T.get(&gid, np));
+    LG_TRY(T.get(&deg, np));
+    size_t stb2 = scan_tmp_bytes(nw > np + 1 ? nw : np + 1) + 64;
+    void* stmp2;
+    LG_TRY(T.get((char**)&stmp2, (int64_t)stb2));
+    LG_TRY(cudaMemsetAsync(bits2, 0, sizeof(uint32_t) * (size_t)nw, s));
+    LG_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int32_t), s));
+    k_mark_priorities<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, pri, 2 * k, n, bits2, sc);
+    LG_TRY(exclusive_popc_scan(bits2, wprefix, nw, stmp2, stb2, s));
+    k_rank<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, pri, bits2, wprefix, nid, gid);
+    k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);
+    LG_TRY(exclusive_scan_i32(deg, g->off, np, nullptr, stmp2, stb2, s));
+    k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, widx, g->dummy_of,
+                                                  gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of);
+    k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
+    LG_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LG_TRY(cudaStreamSynchronize(s));
+    LG_TRY(cudaGetLastError());
+    if (h.err & kEDup) {
+        free_game(g);
+        return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: internal priority collision after preprocessing");
+    }
+#undef LG_TRY
+    pg_status st = alloc_scratch(g);
+    if (st != PG_OK) {
+        free_game(g);
+        return st;
+    }
+    *out = g;
+    return PG_OK;
+}
+
+}  // namespace pg

@@ -1,0 +1,279 @@
+"""Python binding of libpg (include/pg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments: arrays may be numpy arrays or torch tensors
+(CPU tensors and numpy arrays are passed as host memory, CUDA tensors as
+device memory). All computation happens in the CUDA library; if libpg.so is
+missing or fails to load, every call raises ``PgUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpg.so")
+
+PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETIMEOUT, PG_ENOTADMISSIBLE, PG_ECUDA, PG_EUNSUPPORTED = range(7)
+PG_MEM_HOST, PG_MEM_DEVICE = 0, 1
+STATUS_NAMES = {0: "PG_OK", 1: "PG_EINVAL", 2: "PG_ENOMEM", 3: "PG_ETIMEOUT", 4: "PG_ENOTADMISSIBLE",
+                5: "PG_ECUDA", 6: "PG_EUNSUPPORTED"}
+INT32_MAX = 2**31 - 1
+
+
+class PgUnavailable(RuntimeError):
+    pass
+
+
+class PgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class pg_result(C.Structure):
+    _fields_ = [("win", C.c_void_p), ("sigma", C.c_void_p), ("tau", C.c_void_p), ("val_class", C.c_void_p),
+                ("val_depth", C.c_void_p), ("val_rank", C.c_void_p), ("dummy_sigma", C.c_void_p),
+                ("mem_kind", C.c_int32), ("major", C.c_int64), ("inner", C.c_int64)]
+
+
+class pg_solve_opts(C.Structure):
+    _fields_ = [("sigma_init", C.c_void_p), ("tau_init", C.c_void_p), ("dummy_sigma_init", C.c_void_p),
+                ("mem_kind", C.c_int32), ("max_inner", C.c_int64)]
+
+
+class pg_valuation(C.Structure):
+    _fields_ = [("val_class", C.c_void_p), ("val_depth", C.c_void_p), ("val_rank", C.c_void_p),
+                ("dom", C.c_void_p), ("mem_kind", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpg.so (built by paper_1705_02313_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise PgUnavailable("libpg.so is not built: run __graft_entry__.build() or python -m "
+                            "paper_1705_02313_gb300.build")
+    try:
+        L = C.CDLL(LIB_PATH)
+    except OSError as e:
+        raise PgUnavailable("libpg.so failed to load: %s" % e)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    L.pg_ctx_create.argtypes = [C.POINTER(P), C.c_int]
+    L.pg_ctx_destroy.argtypes = [P]
+    L.pg_ctx_destroy.restype = None
+    L.pg_set_stream.argtypes = [P, P]
+    L.pg_last_error.argtypes = [P]
+    L.pg_last_error.restype = C.c_char_p
+    L.pg_load_csr.argtypes = [P, I32, I64, P, P, P, P, I32, C.POINTER(P)]
+    L.pg_game_free.argtypes = [P]
+    L.pg_game_free.restype = None
+    L.pg_game_info.argtypes = [P, C.POINTER(I32), C.POINTER(I64), C.POINTER(I32)]
+    L.pg_game_dummies.argtypes = [P, P]
+    L.pg_solve.argtypes = [P, C.POINTER(pg_solve_opts), C.POINTER(pg_result)]
+    L.pg_best_response.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
+    L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
+    L.pg_set_timing.argtypes = [P, I32]
+    L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(I64)]
+    for name in ["pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing"]:
+        getattr(L, name).restype = I32
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_kind(x):
+    """(pointer, mem_kind) of an array; None gives (None, None)."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (PG_MEM_DEVICE if x.is_cuda else PG_MEM_HOST)
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, PG_MEM_HOST
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(x))
+
+
+def _same_kind(*arrays):
+    kinds = {k for _, k in (_ptr_kind(a) for a in arrays if a is not None)}
+    if len(kinds) > 1:
+        raise ValueError("arrays mix host and device memory")
+    return kinds.pop() if kinds else PG_MEM_HOST
+
+
+def _check(ctx, rc, what):
+    if rc != PG_OK:
+        msg = lib().pg_last_error(ctx).decode(errors="replace") if ctx else what
+        raise PgError(rc, msg)
+
+
+def _dtype_check(x, np_dtype, name):
+    if x is None:
+        return
+    if _is_torch(x):
+        import torch
+        want = {np.int32: torch.int32, np.uint8: torch.uint8, np.int8: torch.int8, np.int64: torch.int64}[np_dtype]
+        if x.dtype != want:
+            raise TypeError("%s must be %s" % (name, want))
+    elif x.dtype != np_dtype:
+        raise TypeError("%s must be %s" % (name, np.dtype(np_dtype)))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as include/pg.h)
+
+def pg_ctx_create(device=0):
+    h = C.c_void_p()
+    rc = lib().pg_ctx_create(C.byref(h), device)
+    if rc != PG_OK:
+        raise PgError(rc, "pg_ctx_create(%d) failed" % device)
+    return h
+
+
+def pg_ctx_destroy(ctx):
+    lib().pg_ctx_destroy(ctx)
+
+
+def pg_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t handle (int), or None."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, lib().pg_set_stream(ctx, C.c_void_p(handle or None)), "pg_set_stream")
+
+
+def pg_last_error(ctx):
+    return lib().pg_last_error(ctx).decode(errors="replace")
+
+
+def pg_load_csr(ctx, n, m, offsets, targets, owner, pri):
+    for a, dt, nm in [(offsets, np.int32, "offsets"), (targets, np.int32, "targets"), (owner, np.uint8, "owner"),
+                      (pri, np.int32, "pri")]:
+        _dtype_check(a, dt, nm)
+    kind = _same_kind(offsets, targets, owner, pri)
+    g = C.c_void_p()
+    rc = lib().pg_load_csr(ctx, int(n), int(m), _ptr_kind(offsets)[0], _ptr_kind(targets)[0], _ptr_kind(owner)[0],
+                           _ptr_kind(pri)[0], kind, C.byref(g))
+    _check(ctx, rc, "pg_load_csr")
+    return g
+
+
+def pg_game_free(game):
+    lib().pg_game_free(game)
+
+
+def pg_game_info(game):
+    n, m, k = C.c_int32(), C.c_int64(), C.c_int32()
+    rc = lib().pg_game_info(game, C.byref(n), C.byref(m), C.byref(k))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_game_info")
+    return n.value, m.value, k.value
+
+
+def pg_game_dummies(game):
+    n, m, k = pg_game_info(game)
+    out = np.zeros(max(k, 1), np.int32)
+    rc = lib().pg_game_dummies(game, out.ctypes.data)
+    if rc != PG_OK:
+        raise PgError(rc, "pg_game_dummies")
+    return out[:k]
+
+
+def pg_solve(ctx, game, win=None, sigma=None, tau=None, val_class=None, val_depth=None, val_rank=None,
+             dummy_sigma=None, sigma_init=None, tau_init=None, dummy_sigma_init=None, max_inner=0):
+    """Fills the given output arrays (all in host memory or all in device
+    memory); returns (major, inner)."""
+    _dtype_check(win, np.uint8, "win")
+    for a, nm in [(sigma, "sigma"), (tau, "tau"), (val_depth, "val_depth"), (val_rank, "val_rank")]:
+        _dtype_check(a, np.int32, nm)
+    _dtype_check(val_class, np.int8, "val_class")
+    _dtype_check(dummy_sigma, np.int8, "dummy_sigma")
+    res = pg_result(_ptr_kind(win)[0], _ptr_kind(sigma)[0], _ptr_kind(tau)[0], _ptr_kind(val_class)[0],
+                    _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dummy_sigma)[0],
+                    _same_kind(win, sigma, tau, val_class, val_depth, val_rank, dummy_sigma), 0, 0)
+    opts = pg_solve_opts(_ptr_kind(sigma_init)[0], _ptr_kind(tau_init)[0], _ptr_kind(dummy_sigma_init)[0],
+                         _same_kind(sigma_init, tau_init, dummy_sigma_init), int(max_inner))
+    rc = lib().pg_solve(game, C.byref(opts), C.byref(res))
+    _check(ctx, rc, "pg_solve")
+    return res.major, res.inner
+
+
+def pg_best_response(ctx, game, sigma, tau_inout=None, dummy_sigma=None, val_class=None, val_depth=None,
+                     val_rank=None, dom=None):
+    _dtype_check(sigma, np.int32, "sigma")
+    _dtype_check(tau_inout, np.int32, "tau_inout")
+    val = pg_valuation(_ptr_kind(val_class)[0], _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dom)[0],
+                       _same_kind(val_class, val_depth, val_rank, dom))
+    iters = C.c_int64(0)
+    rc = lib().pg_best_response(game, _ptr_kind(sigma)[0], _ptr_kind(dummy_sigma)[0], _ptr_kind(tau_inout)[0],
+                                _same_kind(sigma, tau_inout, dummy_sigma), C.byref(val), C.byref(iters))
+    _check(ctx, rc, "pg_best_response")
+    return iters.value
+
+
+def pg_valuate(ctx, game, sigma=None, tau=None, dummy_sigma=None, val_class=None, val_depth=None, val_rank=None,
+               dom=None):
+    """Returns the status code (PG_OK or PG_ENOTADMISSIBLE; outputs are filled in both cases)."""
+    val = pg_valuation(_ptr_kind(val_class)[0], _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dom)[0],
+                       _same_kind(val_class, val_depth, val_rank, dom))
+    rc = lib().pg_valuate(game, _ptr_kind(sigma)[0], _ptr_kind(dummy_sigma)[0], _ptr_kind(tau)[0],
+                          _same_kind(sigma, tau, dummy_sigma), C.byref(val))
+    if rc not in (PG_OK, PG_ENOTADMISSIBLE):
+        _check(ctx, rc, "pg_valuate")
+    return rc
+
+
+def pg_set_timing(ctx, enable):
+    _check(ctx, lib().pg_set_timing(ctx, 1 if enable else 0), "pg_set_timing")
+
+
+def pg_last_timing(game):
+    t, v, s, k = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+    lib().pg_last_timing(game, C.byref(t), C.byref(v), C.byref(s), C.byref(k))
+    return dict(total_ms=t.value, valuation_ms=v.value, switch_ms=s.value, valuations=k.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience: one call from arrays to results (still marshalling only)
+
+def solve_arrays(ctx, n, offsets, targets, owner, pri, device_outputs=False):
+    """Loads, solves and frees a game; returns a dict of numpy (host) or torch
+    (device) arrays plus 'major' and 'inner'."""
+    game = pg_load_csr(ctx, n, int(offsets[-1]), offsets, targets, owner, pri)
+    try:
+        _, _, k = pg_game_info(game)
+        if device_outputs:
+            import torch
+            dev = torch.device("cuda")
+            out = dict(win=torch.empty(n, dtype=torch.uint8, device=dev),
+                       sigma=torch.empty(n, dtype=torch.int32, device=dev),
+                       tau=torch.empty(n, dtype=torch.int32, device=dev),
+                       val_class=torch.empty(n, dtype=torch.int8, device=dev),
+                       val_depth=torch.empty(n, dtype=torch.int32, device=dev),
+                       val_rank=torch.empty(n, dtype=torch.int32, device=dev),
+                       dummy_sigma=torch.empty(max(k, 1), dtype=torch.int8, device=dev))
+        else:
+            out = dict(win=np.empty(n, np.uint8), sigma=np.empty(n, np.int32), tau=np.empty(n, np.int32),
+                       val_class=np.empty(n, np.int8), val_depth=np.empty(n, np.int32),
+                       val_rank=np.empty(n, np.int32), dummy_sigma=np.empty(max(k, 1), np.int8))
+        major, inner = pg_solve(ctx, game, **out)
+        out["dummy_sigma"] = out["dummy_sigma"][:k]
+        out.update(major=major, inner=inner, k=k)
+        return out
+    finally:
+        pg_game_free(game)

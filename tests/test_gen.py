@@ -1,0 +1,62 @@
+"""The seeded generators: determinism, shapes and the structure each workload
+promises (permuted priorities, degree ranges, distinct sorted targets)."""
+import numpy as np
+
+from paper_1705_02313_gb300 import gen
+
+
+def check_csr(g, dmin, dmax):
+    deg = np.diff(g.offsets)
+    assert g.offsets[0] == 0 and (deg >= dmin).all() and (deg <= dmax).all()
+    assert g.targets.min() >= 0 and g.targets.max() < g.n
+    for v in range(min(g.n, 2000)):
+        row = g.targets[g.offsets[v]:g.offsets[v + 1]]
+        assert (np.diff(row) > 0).all()
+
+
+def test_random_game_shape_and_determinism():
+    a = gen.random_game(5000, 2, 8, seed=3)
+    b = gen.random_game(5000, 2, 8, seed=3)
+    c = gen.random_game(5000, 2, 8, seed=4)
+    for x, y in zip(a.arrays(), b.arrays()):
+        assert np.array_equal(x, y)
+    assert not np.array_equal(a.targets, c.targets)
+    check_csr(a, 2, 8)
+    assert sorted(a.pri.tolist()) == list(range(a.n))
+    assert 0.45 < a.owner.mean() < 0.55
+
+
+def test_splitmix64_published_values():
+    # SplitMix64 from state 0: first outputs of the published generator
+    z = gen.splitmix64(np.uint64(0))
+    assert int(z) == 0xE220A8397B1DCDAF
+    z2 = gen.splitmix64(gen.GOLDEN)
+    assert int(z2) == 0x6E789E6AA1B965F4
+
+
+def test_ladder_and_chain():
+    g = gen.ladder_game(1000, 1)
+    check_csr(g, 1, 2)
+    assert g.targets[0] == 1
+    for i in range(1, 999):
+        row = g.targets[g.offsets[i]:g.offsets[i + 1]]
+        assert row[1] == i + 1 and row[0] < i
+    game, sigma = gen.chain_profile(1000, 2)
+    check_csr(game, 1, 3)
+    assert (sigma == -1).sum() == 1
+    # sigma follows existing edges and visits every vertex once
+    x = int(np.nonzero(np.bincount(sigma[sigma >= 0], minlength=1000) == 0)[0][0])
+    seen = 0
+    while x != -1:
+        seen += 1
+        nxt = sigma[x]
+        if nxt >= 0:
+            assert nxt in game.targets[game.offsets[x]:game.offsets[x + 1]]
+        x = nxt
+    assert seen == 1000
+
+
+def test_log_uniform_sizes():
+    s = gen.log_uniform_sizes(4096, 1000, 1_000_000)
+    assert s.min() >= 1000 and s.max() <= 1_000_000
+    assert 100_000 < s.mean() < 200_000
