@@ -1,0 +1,424 @@
+"""Benchmark: greedy all-switches strategy improvement on one 10M-vertex game.
+
+One step = one whole solve through the C ABI: pg_load_csr from device-resident
+input arrays (validation, the admissibility preprocessing and relabelling on
+the GPU) followed by pg_solve to device-resident results (every inner and
+outer iteration of Algorithm 1). The reported value is best-response edges/s:
+input edges times valuations computed, divided by the step time (the whole
+step, preprocessing and Even switches included).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): every rank solves its own replica
+of the game (a single game does not shard: replicas only); value = edges *
+valuations summed over ranks / the slowest rank's time.
+--impl reference times the CPU oracle (oracle/o2.c, single thread) on a
+bounded sample of the same workload: each step runs the first iterations of
+the same solve.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "best-response edges/s (10M-vertex random parity game, full solve)"
+UNIT = "edges/s"
+WORKLOADS = {
+    # name: (generator, kwargs, description)
+    "random-10m": ("random_game", dict(n=10_000_000, dmin=2, dmax=5, seed=0),
+                   "random game, n=10,000,000, out-degree U[2,5], owners p=0.5, permuted priorities, seed 0"),
+    "random-1m": ("random_game", dict(n=1_000_000, dmin=2, dmax=8, seed=0),
+                  "random game, n=1,000,000, out-degree U[2,8], owners p=0.5, permuted priorities, seed 0"),
+    "ladder-10m": ("ladder_game", dict(n=10_000_000, seed=0),
+                   "ladder game, n=10,000,000, i->i+1 plus one back edge, owners p=0.5, permuted priorities"),
+}
+
+
+def make_game(name):
+    from paper_1705_02313_gb300 import gen
+    fn, kw, _ = WORKLOADS[name]
+    kw = dict(kw)
+    if fn == "random_game":
+        return gen.random_game(kw["n"], kw["dmin"], kw["dmax"], kw["seed"])
+    return gen.ladder_game(kw["n"], kw["seed"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# per-kernel algorithmic bytes (the compulsory traffic of each pass)
+
+def algorithmic_bytes(name, s):
+    n, m = s["n"], s["m"]
+    if name == "walk":
+        return 12 * n
+    if name == "chain1":
+        return 15 * n
+    if name == "parents":
+        return 8 * n
+    if name == "sink_scan":
+        return 16 * n
+    if name == "chain2":
+        return 29 * n
+    if name == "switch_odd":
+        return n + 12 * s["n_odd"] + 8 * s["m_odd"]
+    if name == "switch_even":
+        return n + 16 * s["n_even"] + 8 * s["m_even"]
+    return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1705_02313_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1705_02313_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload):
+    """dram bytes per launch of ``kernel`` from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[workload][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+
+def cpu_sample(game, iters):
+    from oracle import o2
+    gp = o2.preprocess(game.n, game.offsets, game.targets, game.owner, game.pri)
+    t0 = time.perf_counter()
+    res = o2.run(gp, max_inner=iters, allow_timeout=True)
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, iters=res["inner"], edges=game.m)
+
+
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    game = make_game(args.workload)
+    iters = args.ref_iters
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_sample(game, iters)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+    tot = sum(times)
+    value = game.m * iters * len(times) / tot
+    sample = "first %d valuations (of a full solve) of the %s workload per step" % (iters, args.workload)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2], "n": game.n, "m": game.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1705_02313_gb300 import build
+    build.build()
+    from paper_1705_02313_gb300 import pg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    game = make_game(args.workload)
+    n, m = game.n, game.m
+    ctx = pg.pg_ctx_create(local)
+    stream = torch.cuda.Stream(device=dev)
+    pg.pg_set_stream(ctx, stream)
+    d_in = [torch.from_numpy(a).to(dev) for a in game.arrays()]
+    torch.cuda.synchronize()
+    out = dict(win=torch.empty(n, dtype=torch.uint8, device=dev), sigma=torch.empty(n, dtype=torch.int32, device=dev),
+               tau=torch.empty(n, dtype=torch.int32, device=dev), val_class=torch.empty(n, dtype=torch.int8, device=dev),
+               val_depth=torch.empty(n, dtype=torch.int32, device=dev),
+               val_rank=torch.empty(n, dtype=torch.int32, device=dev))
+
+    def step(inputs, outputs):
+        g = pg.pg_load_csr(ctx, n, m, *inputs)
+        try:
+            _, _, k = pg.pg_game_info(g)
+            like = outputs["win"]
+            if like.is_cuda:
+                ds = torch.empty(max(k, 1), dtype=torch.int8, device=like.device)
+            else:
+                ds = torch.empty(max(k, 1), dtype=torch.int8).pin_memory()
+            major, inner = pg.pg_solve(ctx, g, dummy_sigma=ds, **outputs)
+            stats = pg.pg_kernel_stats(g)
+            return major, inner, k, stats, pg.pg_last_timing(g)
+        finally:
+            pg.pg_game_free(g)
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        step(d_in, out)
+    # per-kernel timing pass (untimed): device time of each kernel class
+    pg.pg_set_timing(ctx, True)
+    major, inner, k, kstats, tinfo = step(d_in, out)
+    pg.pg_set_timing(ctx, False)
+
+    # timed region: K steps, inputs resident in HBM, results to HBM
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = pg.pg_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    inner_total = 0
+    for _ in range(args.steps):
+        _, inner_s, _, _, _ = step(d_in, out)
+        inner_total += inner_s
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    dev_ms = ev0.elapsed_time(ev1)
+    launches = pg.pg_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    t_ms = max(dev_ms, 0.0)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms, float(inner_total)], device=dev, dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t_ms, inner_sum = float(mx[0]), float(sm[1])
+    else:
+        inner_sum = float(inner_total)
+    value = m * inner_sum / (t_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: pinned inputs, pinned outputs
+    h_in = [torch.from_numpy(a).pin_memory() for a in game.arrays()]
+    h_out = {kk: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for kk, v in out.items()}
+    step(h_in, h_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_inner = 0
+    for _ in range(args.steps):
+        _, i_s, _, _, _ = step(h_in, h_out)
+        e_inner += i_s
+    torch.cuda.synchronize()
+    e_wall = time.perf_counter() - t0
+    h2d = sum(a.nbytes for a in game.arrays())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + k
+    e2e = {"value": m * e_inner / e_wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant kernel class
+    own = game.owner
+    deg = np.diff(game.offsets).astype(np.int64)
+    s = {"n": n + k, "m": m + k, "n_odd": int(own.sum()), "m_odd": int(deg[own == 1].sum()),
+         "n_even": int((own == 0).sum()) + k, "m_even": int(deg[own == 0].sum()) + k}
+    per = {nm: (ms, launches_k, calls) for nm, (ms, launches_k, calls) in kstats.items() if calls > 0}
+    dom_name = max(per, key=lambda x: per[x][0]) if per else None
+    hbm, src = peaks()
+    roof = None
+    if dom_name:
+        ms, _, calls = per[dom_name]
+        avg_s = ms / calls / 1000.0
+        ab = algorithmic_bytes(dom_name, s)
+        ach = ab / avg_s / 1e9 if ab else None
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": (ach / hbm if ach else None), "peak_source": src + " (hbm_gbs, burst copy)",
+                "traffic": measured_traffic(dom_name, args.workload),
+                "algorithmic_bytes_per_launch": ab, "avg_launch_us": avg_s * 1e6}
+    valuation_path = None
+    if tinfo["valuations"]:
+        per_iter_s = (tinfo["valuation_ms"] + tinfo["switch_ms"]) / tinfo["valuations"] / 1000.0
+        b_alg = 8 * (m + k) + 20 * (n + k)
+        valuation_path = {"inner_iteration_us": per_iter_s * 1e6, "b_alg_bytes": b_alg,
+                          "achieved_gbs": b_alg / per_iter_s / 1e9, "frac_of_hbm": b_alg / per_iter_s / 1e9 / hbm,
+                          "inner_loop_edges_per_s": m / per_iter_s}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2], "n": n, "m": m,
+                   "dummies": k, "valuations_per_solve": inner, "major_iterations": major,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (CSR %.0f MB; no flush)" % (h2d / 1e6)},
+        "full_solve_ms": t_ms / args.steps,
+        "wall_s": wall,
+        "roofline": roof,
+        "inner_iteration": valuation_path,
+        "kernels": {nm: {"ms": v[0], "launches": v[1], "calls": v[2]} for nm, v in kstats.items() if v[1]},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        r = cpu_sample(game, args.cpu_iters)
+        line["cpu_baseline"] = {"value": r["edges"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": "first %d valuations of the same solve (%.1f s single-threaded)" %
+                                          (r["iters"], r["seconds"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pg.pg_ctx_destroy(ctx)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_solves(args):
+    """Only W warm-up solves plus ``--profile-solves`` solves of the workload
+    (no timing region, no baselines): the command that profiler captures run."""
+    import torch
+
+    from paper_1705_02313_gb300 import build
+    build.build()
+    from paper_1705_02313_gb300 import pg
+    game = make_game(args.workload)
+    n, m = game.n, game.m
+    ctx = pg.pg_ctx_create(0)
+    pg.pg_set_timing(ctx, True)
+    d_in = [torch.from_numpy(a).cuda() for a in game.arrays()]
+    out = dict(win=torch.empty(n, dtype=torch.uint8, device="cuda"))
+    res = []
+    for i in range(args.profile_solves):
+        g = pg.pg_load_csr(ctx, n, m, *d_in)
+        try:
+            major, inner = pg.pg_solve(ctx, g, **out)
+            res.append({"major": major, "inner": inner, "kernels_ms": {k: round(v[0], 3) for k, v in
+                                                                       pg.pg_kernel_stats(g).items() if v[1]}})
+        finally:
+            pg.pg_game_free(g)
+    print(json.dumps({"workload": args.workload, "solves": res}), flush=True)
+    pg.pg_ctx_destroy(ctx)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="run only this many solves (for profiler captures) and exit")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random-10m")
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--ref-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.profile_solves:
+        return run_profile_solves(args)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -153,6 +153,25 @@ pg_status pg_best_response(pg_game *game, const int32_t *sigma, const int8_t *du
 pg_status pg_valuate(pg_game *game, const int32_t *sigma, const int8_t *dummy_sigma, const int32_t *tau,
                      int32_t mem_kind, pg_valuation *out);
 
+/* Device time per kernel class, accumulated over calls since pg_reset_stats
+ * (times only while timing is enabled; launch counts always). name is the
+ * class (walk, jump, chain1, parents, big_parents, sink_scan, chain2,
+ * switch_odd, switch_even); calls counts timed event pairs, launches counts
+ * kernels. out has room for cap entries (host memory); count receives the
+ * number of classes. The paper reports wall-clock time only (Section 6); this
+ * breakdown has no counterpart there. */
+typedef struct {
+    char name[24];
+    double ms;
+    int64_t launches;
+    int64_t calls;
+} pg_kernel_stat;
+pg_status pg_kernel_stats(const pg_game *game, pg_kernel_stat *out, int32_t cap, int32_t *count);
+pg_status pg_reset_stats(pg_game *game);
+
+/* Number of kernels launched through ctx since it was created. */
+pg_status pg_launch_count(const pg_ctx *ctx, int64_t *out);
+
 /* Per-phase device time of the last pg_solve / pg_best_response / pg_valuate
  * on game, in milliseconds, measured with CUDA events on the context's stream
  * when timing is enabled (pg_set_timing). Each pointer may be NULL. */

@@ -74,9 +74,10 @@ def initial_profile(gp):
     return strat.astype(np.int32)
 
 
-def run(gp, strat=None, mode="solve", max_inner=10**9, check=False, stats_cap=0):
+def run(gp, strat=None, mode="solve", max_inner=10**9, check=False, stats_cap=0, allow_timeout=False):
     """Algorithm 1 (Section 4) on the preprocessed game. Raises OracleError
-    for any non-OK status; ``res['status']`` is always OK on return."""
+    for any non-OK status (except the iteration cap when ``allow_timeout``);
+    ``res['status']`` holds the status."""
     n = gp["n"]
     strat = initial_profile(gp) if strat is None else np.array(strat, dtype=np.int32, copy=True)
     cls = np.zeros(n, np.int8)
@@ -91,9 +92,9 @@ def run(gp, strat=None, mode="solve", max_inner=10**9, check=False, stats_cap=0)
                       0 if mode == "solve" else 1, int(max_inner), 1 if check else 0,
                       _p(cls), _p(depth), _p(rank), _p(dom), C.byref(sink_rank), C.byref(major), C.byref(inner),
                       _p(stats) if stats_cap else None, int(stats_cap))
-    if rc:
+    if rc and not (allow_timeout and rc == ETIMEOUT):
         raise OracleError(rc, "o2_run")
-    res = dict(strat=strat, cls=cls, depth=depth, rank=rank, dom=dom, sink_rank=sink_rank.value,
+    res = dict(status=rc, strat=strat, cls=cls, depth=depth, rank=rank, dom=dom, sink_rank=sink_rank.value,
                major=major.value, inner=inner.value)
     if stats_cap:
         res["stats"] = stats[: 4 * min(inner.value, stats_cap)].reshape(-1, 4)

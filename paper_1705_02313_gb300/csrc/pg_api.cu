@@ -31,6 +31,8 @@ void free_game(pg_game* g) {
         if (p) cudaFree(p);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : g->kev)
+        if (e) cudaEventDestroy(e);
     delete g;
 }
 
@@ -152,6 +154,7 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
              vdepth ? (int32_t*)(b + L.off_depth) : nullptr, vrank ? (int32_t*)(b + L.off_rank) : nullptr,
              vdom ? (int32_t*)(b + L.off_dom) : nullptr,     dsig ? (int8_t*)(b + L.off_dsig) : nullptr};
     }
+    ctx->launches += 1;
     k_results<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->dnid, g->flags,
                                                                 g->strat, g->cls, g->depth, g->key, g->orig_of,
                                                                 g->dom, o);
@@ -202,6 +205,7 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
     int32_t* err = &g->cnt->err;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) {
+        ctx->launches += 1;
         k_apply_profile<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->off, g->tgt,
                                                                           g->flags, g->orig_of, g->dnid, ds, dt, dd,
                                                                           g->strat, err);
@@ -310,6 +314,37 @@ pg_status pg_last_timing(const pg_game* g, double* total_ms, double* valuation_m
     if (valuation_ms) *valuation_ms = g->t_val;
     if (switch_ms) *switch_ms = g->t_switch;
     if (valuations) *valuations = g->t_vals;
+    return PG_OK;
+}
+
+pg_status pg_kernel_stats(const pg_game* g, pg_kernel_stat* out, int32_t cap, int32_t* count) {
+    if (!g || (!out && cap > 0)) return PG_EINVAL;
+    int32_t c = 0;
+    for (int id = 0; id < KID_COUNT && c < cap; ++id, ++c) {
+        memset(out[c].name, 0, sizeof(out[c].name));
+        strncpy(out[c].name, kKernelNames[id], sizeof(out[c].name) - 1);
+        out[c].ms = g->kms[id];
+        out[c].launches = g->klaunch[id];
+        out[c].calls = g->kcalls[id];
+    }
+    if (count) *count = KID_COUNT;
+    return PG_OK;
+}
+
+pg_status pg_reset_stats(pg_game* g) {
+    if (!g) return PG_EINVAL;
+    for (int id = 0; id < KID_COUNT; ++id) {
+        g->kms[id] = 0;
+        g->klaunch[id] = 0;
+        g->kcalls[id] = 0;
+        g->kpend[id] = false;
+    }
+    return PG_OK;
+}
+
+pg_status pg_launch_count(const pg_ctx* ctx, int64_t* out) {
+    if (!ctx || !out) return PG_EINVAL;
+    *out = ctx->launches;
     return PG_OK;
 }
 

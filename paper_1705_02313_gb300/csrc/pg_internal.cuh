@@ -67,7 +67,20 @@ struct Counters {
 constexpr int32_t kErrTooManyChildren = 1;
 constexpr int32_t kErrJumpRounds = 2;
 
-struct Game;
+// Kernel classes of one iteration, for per-kernel device timing.
+enum KernelId {
+    KID_WALK,        // k_gwalk
+    KID_JUMP,        // k_jump rounds
+    KID_CHAIN1,      // k_chain1
+    KID_PARENTS,     // k_parents
+    KID_BIG,         // big-parent passes
+    KID_SINKSCAN,    // the sink's id-ordered scan (3 kernels)
+    KID_CHAIN2,      // k_chain2
+    KID_SWITCH_ODD,  // k_switch for Odd
+    KID_SWITCH_EVEN, // k_switch for Even
+    KID_COUNT
+};
+extern const char* const kKernelNames[KID_COUNT];
 
 // scan helpers (pg_scan.cu)
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total; int64 accumulation, int32 output.
@@ -90,6 +103,7 @@ struct pg_ctx {
     std::string err = "no error";
     bool timing = false;
     int32_t* pinned = nullptr;  // small pinned host buffer for counters
+    int64_t launches = 0;       // kernels launched through this context
 };
 
 struct pg_game {
@@ -136,6 +150,12 @@ struct pg_game {
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per-kernel-class device time (timing enabled) and launch counts
+    double kms[pg::KID_COUNT] = {};
+    int64_t klaunch[pg::KID_COUNT] = {};
+    int64_t kcalls[pg::KID_COUNT] = {};
+    cudaEvent_t kev[2 * pg::KID_COUNT] = {};
+    bool kpend[pg::KID_COUNT] = {};
 };
 
 // internal entry points shared by the translation units
@@ -146,6 +166,10 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const
                     const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out);
 pg_status alloc_scratch(pg_game* g);
 void free_game(pg_game* g);
+// per-kernel timing: events around a kernel class on the game's stream
+void prof_begin(pg_game* g, int id);
+void prof_end(pg_game* g, int id, int nlaunch);
+void prof_collect(pg_game* g);  // after a stream synchronisation
 // one valuation of g->strat: fills cls, depth, key (and dom when want_dom). Returns counters on host.
 pg_status valuate_device(pg_game* g, bool want_dom, Counters* host_cnt);
 // one switching pass for player (0 Even, 1 Odd) using g->key; returns switched count.

@@ -575,6 +575,34 @@ __global__ void k_switch(int32_t n, int player, const int32_t* __restrict__ off,
 
 }  // namespace
 
+const char* const kKernelNames[KID_COUNT] = {"walk", "jump", "chain1", "parents", "big_parents",
+                                              "sink_scan", "chain2", "switch_odd", "switch_even"};
+
+void prof_begin(pg_game* g, int id) {
+    if (g->ctx->timing) cudaEventRecord(g->kev[2 * id], g->ctx->stream);
+}
+
+void prof_end(pg_game* g, int id, int nlaunch) {
+    g->ctx->launches += nlaunch;
+    g->klaunch[id] += nlaunch;
+    if (g->ctx->timing) {
+        cudaEventRecord(g->kev[2 * id + 1], g->ctx->stream);
+        g->kpend[id] = true;
+    }
+}
+
+void prof_collect(pg_game* g) {
+    for (int id = 0; id < KID_COUNT; ++id) {
+        if (!g->kpend[id]) continue;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, g->kev[2 * id], g->kev[2 * id + 1]) == cudaSuccess) {
+            g->kms[id] += ms;
+            g->kcalls[id] += 1;
+        }
+        g->kpend[id] = false;
+    }
+}
+
 pg_status alloc_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     int64_t n = g->n;
@@ -605,6 +633,7 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->tile_e, 0xff, sizeof(int32_t) * n, s));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->tile_o, 0, sizeof(int32_t) * n, s));
     for (int i = 0; i < 4; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->ev[i]));
+    for (int i = 0; i < 2 * KID_COUNT; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->kev[i]));
     return PG_OK;
 }
 
@@ -615,9 +644,12 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
     Counters* c = g->cnt;
     unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
+    prof_begin(g, KID_WALK);
     k_gwalk<<<grid, kBlock, 0, s>>>(n, g->strat, g->gd, g->plist, c);
+    prof_end(g, KID_WALK, 1);
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_pending, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    prof_collect(g);
     int32_t np = ctx->pinned[0];
     if (np > 0) {
         int rounds = 0;
@@ -625,16 +657,23 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
         for (;;) {
             PG_CUDA_TRY(ctx, cudaMemsetAsync(&c->n_pending, 0, sizeof(int32_t), s));
+            prof_begin(g, KID_JUMP);
             k_jump<<<grid_for(np), kBlock, 0, s>>>(np, g->plist, g->gd, c);
+            prof_end(g, KID_JUMP, 1);
             PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_pending, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            prof_collect(g);
             if (ctx->pinned[0] == 0) break;
             if (++rounds > cap) return fail(ctx, PG_ECUDA, "valuation: pointer jumping did not converge");
         }
     }
+    prof_begin(g, KID_CHAIN1);
     k_chain1<<<grid, kBlock, 0, s>>>(n, g->gd, g->flags, g->pri, g->cls, g->kind, g->depth, g->sz, g->head, g->nxt,
                                      g->dom, want_dom ? 1 : 0, c);
+    prof_end(g, KID_CHAIN1, 1);
+    prof_begin(g, KID_PARENTS);
     k_parents<<<grid, kBlock, 0, s>>>(n, g->head, g->nxt, g->sz, g->flags, g->wgt, g->oddsz, g->biglist, c);
+    prof_end(g, KID_PARENTS, 1);
     int32_t* bigslot = g->tile_e;
     int32_t* bigfill = g->tile_o;
     int32_t* hugelist = g->plist;  // pending list is no longer needed
@@ -643,6 +682,7 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
     int32_t* bigbuf = g->key;
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_big, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    prof_collect(g);
     int32_t nbig = ctx->pinned[0];
     if (nbig > 0) {
         int64_t cap_parents = (int64_t)n / kBlockChildren;
@@ -660,12 +700,15 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
                                              cudaMemcpyHostToDevice, s));
             PG_CUDA_TRY(ctx, cudaMemcpyAsync(&c->n_big, &cnt_b, sizeof(int32_t), cudaMemcpyHostToDevice, s));
             PG_CUDA_TRY(ctx, cudaMemsetAsync(&c->pad, 0, sizeof(int32_t), s));
+            prof_begin(g, KID_BIG);
             k_big_mark<<<grid_for(cnt_b), kBlock, 0, s>>>(g->biglist, bigslot, c);
             k_big_collect<<<grid, kBlock, 0, s>>>(n, g->gd, g->kind, bigslot, bigfill, bigbuf, c);
             k_big_parents<<<(unsigned)std::min<int64_t>(cnt_b, 152 * 4), kBlock, 0, s>>>(
                 g->biglist, bigslot, bigfill, bigbuf, g->sz, g->flags, g->wgt, g->oddsz, hugelist, c);
+            prof_end(g, KID_BIG, 3);
             PG_CUDA_TRY(ctx, cudaMemcpyAsync(&hc, c, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            prof_collect(g);
             if (hc.pad > 0) {
                 size_t old = huge.size();
                 huge.resize(old + hc.pad);
@@ -676,6 +719,7 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
         }
         // huge parents: one id-ordered scan each
         for (int32_t p : huge) {
+            ctx->launches += 3;
             k_idscan_reduce<false><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, p, g->kind, g->gd, g->sz, g->flags,
                                                                           g->scan_total);
             k_idscan_tiles<<<1, kBlock, 0, s>>>(g->scan_total, g->ntiles);
@@ -685,14 +729,19 @@ pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
         }
     }
     // the sink's children
+    prof_begin(g, KID_SINKSCAN);
     k_idscan_reduce<true><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, n, g->kind, g->gd, g->sz, g->flags,
                                                                  g->scan_total);
     k_idscan_tiles<<<1, kBlock, 0, s>>>(g->scan_total, g->ntiles);
     k_idscan_apply<true><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, n, g->kind, g->gd, g->sz, g->flags,
                                                                 g->scan_total, g->ntiles, g->wgt, &c->sink_rank);
+    prof_end(g, KID_SINKSCAN, 3);
+    prof_begin(g, KID_CHAIN2);
     k_chain2<<<grid, kBlock, 0, s>>>(n, g->gd, g->kind, g->wgt, g->oddsz, g->key, g->sz, g->head, c);
+    prof_end(g, KID_CHAIN2, 1);
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(h, c, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    prof_collect(g);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
@@ -701,9 +750,13 @@ pg_status switch_device(pg_game* g, int player, int32_t* nswitch) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
+    int kid = player ? KID_SWITCH_ODD : KID_SWITCH_EVEN;
+    prof_begin(g, kid);
     k_switch<<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->key, g->strat, g->cnt);
+    prof_end(g, kid, 1);
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &g->cnt->n_switch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    prof_collect(g);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     *nswitch = ctx->pinned[0];
     return PG_OK;

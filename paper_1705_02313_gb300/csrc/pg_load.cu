@@ -221,6 +221,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         LoadScalars init = {0, -1, 0, 0};
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     }
+    ++ctx->launches;
     k_validate<<<nblocks(n), kBlock, 0, s>>>(n, m, off, tgt, own, pri, sc);
     LoadScalars h;
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -237,6 +238,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         uint32_t* bits;
         PG_CUDA_TRY(ctx, T.get(&bits, nwords));
         PG_CUDA_TRY(ctx, cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)nwords, s));
+        ++ctx->launches;
         k_mark_priorities<<<nblocks(n), kBlock, 0, s>>>(n, pri, 0, n, bits, sc);
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
         PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -255,9 +257,12 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, T.get(&radj, m));
     PG_CUDA_TRY(ctx, T.get(&fill, (int64_t)n + 1));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (size_t)n, s));
+    ++ctx->launches;
     k_indegree<<<nblocks(m), kBlock, 0, s>>>(m, tgt, indeg);
+    ctx->launches += 3;
     PG_CUDA_TRY(ctx, exclusive_scan_i32(indeg, roff, n, nullptr, stmp, stb, s));
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(fill, roff, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+    ++ctx->launches;
     k_reverse_scatter<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, fill, radj);
 
     // U: greatest fixpoint by peeling
@@ -265,6 +270,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, T.get(&fa, n));
     PG_CUDA_TRY(ctx, T.get(&fb, n));
     PG_CUDA_TRY(ctx, T.get(&inU, n));
+    ++ctx->launches;
     k_trap_init<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, inU, cnt, fa, sc);
     for (int64_t round = 0;; ++round) {
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -273,6 +279,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         if (nf == 0) break;
         if (round > n) return fail(ctx, PG_EINVAL, "pg_load_csr: trap peeling did not converge");
         PG_CUDA_TRY(ctx, cudaMemsetAsync(&sc->frontier, 0, sizeof(int32_t), s));
+        ++ctx->launches;
         k_trap_peel<<<nblocks(nf), kBlock, 0, s>>>(nf, fa, roff, radj, own, inU, cnt, fb, sc);
         int32_t* t = fa;
         fa = fb;
@@ -281,7 +288,9 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, T.get(&isW, n));
     PG_CUDA_TRY(ctx, T.get(&widx, (int64_t)n + 1));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(isW, 0, (size_t)n, s));
+    ++ctx->launches;
     k_mark_w<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, inU, isW);
+    ctx->launches += 3;
     PG_CUDA_TRY(ctx, exclusive_scan_u8(isW, widx, n, stmp, stb, s));
     int32_t k = 0;
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(&k, widx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -317,6 +326,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     LG_TRY(dalloc(&g->dnid, k));
     LG_TRY(dalloc(&g->dummy_of, k));
     LG_TRY(dalloc(&g->strat, np));
+    ++ctx->launches;
     k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
 
     // ranks of the G' priorities
@@ -334,13 +344,20 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     LG_TRY(T.get((char**)&stmp2, (int64_t)stb2));
     LG_TRY(cudaMemsetAsync(bits2, 0, sizeof(uint32_t) * (size_t)nw, s));
     LG_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int32_t), s));
+    ++ctx->launches;
     k_mark_priorities<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, pri, 2 * k, n, bits2, sc);
+    ctx->launches += 3;
     LG_TRY(exclusive_popc_scan(bits2, wprefix, nw, stmp2, stb2, s));
+    ++ctx->launches;
     k_rank<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, pri, bits2, wprefix, nid, gid);
+    ++ctx->launches;
     k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);
+    ctx->launches += 3;
     LG_TRY(exclusive_scan_i32(deg, g->off, np, nullptr, stmp2, stb2, s));
+    ++ctx->launches;
     k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, widx, g->dummy_of,
                                                   gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of);
+    ++ctx->launches;
     k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
     LG_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
     LG_TRY(cudaStreamSynchronize(s));

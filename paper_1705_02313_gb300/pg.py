@@ -49,6 +49,10 @@ class pg_valuation(C.Structure):
                 ("dom", C.c_void_p), ("mem_kind", C.c_int32)]
 
 
+class pg_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("ms", C.c_double), ("launches", C.c_int64), ("calls", C.c_int64)]
+
+
 _lib = None
 
 
@@ -82,7 +86,10 @@ def lib():
     L.pg_set_timing.argtypes = [P, I32]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(I64)]
-    for name in ["pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
+    L.pg_kernel_stats.argtypes = [P, C.POINTER(pg_kernel_stat), I32, C.POINTER(I32)]
+    L.pg_reset_stats.argtypes = [P]
+    L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
+    for name in ["pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -246,6 +253,28 @@ def pg_last_timing(game):
     t, v, s, k = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
     lib().pg_last_timing(game, C.byref(t), C.byref(v), C.byref(s), C.byref(k))
     return dict(total_ms=t.value, valuation_ms=v.value, switch_ms=s.value, valuations=k.value)
+
+
+def pg_kernel_stats(game):
+    """{name: (ms, launches, calls)} per kernel class since pg_reset_stats."""
+    arr = (pg_kernel_stat * 32)()
+    cnt = C.c_int32(0)
+    rc = lib().pg_kernel_stats(game, arr, 32, C.byref(cnt))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_kernel_stats")
+    return {arr[i].name.decode(): (arr[i].ms, arr[i].launches, arr[i].calls) for i in range(min(cnt.value, 32))}
+
+
+def pg_reset_stats(game):
+    rc = lib().pg_reset_stats(game)
+    if rc != PG_OK:
+        raise PgError(rc, "pg_reset_stats")
+
+
+def pg_launch_count(ctx):
+    out = C.c_int64(0)
+    _check(ctx, lib().pg_launch_count(ctx, C.byref(out)), "pg_launch_count")
+    return out.value
 
 
 # ---------------------------------------------------------------------------
