@@ -41,6 +41,9 @@ WORKLOADS = {
                    "random game, n=10,000,000, out-degree U[2,5], owners p=0.5, permuted priorities, seed 0"),
     "random-1m": ("random_game", dict(n=1_000_000, dmin=2, dmax=8, seed=0),
                   "random game, n=1,000,000, out-degree U[2,8], owners p=0.5, permuted priorities, seed 0"),
+    "random-6m": ("random_game", dict(n=6_000_000, dmin=2, dmax=5, seed=0),
+                  "random game, n=6,000,000, out-degree U[2,5], owners p=0.5, permuted priorities, seed 0 "
+                  "(profiling case: inputs above L2, about 1 GB on the device)"),
     "ladder-10m": ("ladder_game", dict(n=10_000_000, seed=0),
                    "ladder game, n=10,000,000, i->i+1 plus one back edge, owners p=0.5, permuted priorities"),
 }
