@@ -23,12 +23,13 @@ pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where) {
 
 void free_game(pg_game* g) {
     if (!g) return;
-    void* ptrs[] = {g->off,  g->tgt,   g->flags, g->pri,   g->nid0,    g->orig_of, g->dnid, g->dummy_of,
-                    g->strat, g->gd,   g->plist, g->cls,   g->kind,    g->depth,   g->sz,   g->head,
-                    g->nxt,  g->wgt,   g->oddsz, g->key,   g->dom,     g->biglist, g->cnt,  g->scan_total,
-                    g->tile_e, g->tile_o, g->stage};
+    void* ptrs[] = {g->off,  g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
+                    g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
+                    g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
+                    g->tiles, g->cnt,    g->scan_tmp, g->stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (g->hcnt) cudaFreeHost(g->hcnt);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : g->kev)
@@ -154,6 +155,10 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
              vdepth ? (int32_t*)(b + L.off_depth) : nullptr, vrank ? (int32_t*)(b + L.off_rank) : nullptr,
              vdom ? (int32_t*)(b + L.off_dom) : nullptr,     dsig ? (int8_t*)(b + L.off_dsig) : nullptr};
     }
+    if (vdepth) {
+        pg_status st = enqueue_depth(g);
+        if (st) return st;
+    }
     ctx->launches += 1;
     k_results<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->dnid, g->flags,
                                                                 g->strat, g->cls, g->depth, g->key, g->orig_of,
@@ -238,7 +243,8 @@ struct Timer {
 };
 
 // The inner loop of Algorithm 1: valuations and Odd switches until no Odd
-// vertex switches. The last valuation is left in g (key, cls, depth).
+// vertex switches. The last valuation is left in g (key, cls, depth). One
+// host synchronisation per iteration (the switch count).
 pg_status inner_loop(pg_game* g, int64_t cap, int64_t* inner, Timer& tm, bool* timed_out) {
     *timed_out = false;
     for (;;) {
@@ -246,21 +252,21 @@ pg_status inner_loop(pg_game* g, int64_t cap, int64_t* inner, Timer& tm, bool* t
             *timed_out = true;
             return PG_OK;
         }
-        Counters hc;
         tm.mark(0);
-        pg_status st = valuate_device(g, false, &hc);
+        pg_status st = enqueue_valuation(g, false);
         if (st) return st;
         tm.mark(1);
-        ++*inner;
-        if (hc.n_odd > 0)
-            return fail(g->ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
-        int32_t nsw = 0;
-        st = switch_device(g, 1, &nsw);
+        st = enqueue_switch(g, 1);
         if (st) return st;
         tm.mark(2);
+        st = sync_counters(g);
+        if (st) return st;
+        ++*inner;
         g->t_val += tm.since(0, 1);
         g->t_switch += tm.since(1, 2);
-        if (nsw == 0) return PG_OK;
+        if (g->hcnt->n_odd > 0)
+            return fail(g->ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
+        if (g->hcnt->n_switch == 0) return PG_OK;
     }
 }
 
@@ -381,6 +387,8 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     pg_status st = apply_profile(g, opts ? opts->sigma_init : nullptr, opts ? opts->tau_init : nullptr,
                                  opts ? opts->dummy_sigma_init : nullptr, opts ? opts->mem_kind : PG_MEM_HOST);
     if (st) return st;
+    st = reset_scratch(g);
+    if (st) return st;
     Timer tm(g);
     tm.mark(3);
     int64_t major = 0, inner = 0;
@@ -389,15 +397,16 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
         st = inner_loop(g, cap, &inner, tm, &timed_out);
         if (st) return st;
         if (timed_out) break;
-        int32_t nsw = 0;
-        st = switch_device(g, 0, &nsw);
+        st = enqueue_switch(g, 0);
         if (st) return st;
-        if (nsw == 0) break;
+        st = sync_counters(g);
+        if (st) return st;
+        if (g->hcnt->n_switch == 0) break;
         ++major;
     }
     if (timed_out) {
-        Counters hc;
-        st = valuate_device(g, false, &hc);  // valuation of the profile being returned
+        st = enqueue_valuation(g, false);  // valuation of the profile being returned
+        if (!st) st = sync_counters(g);
         if (st) return st;
     }
     tm.mark(2);
@@ -419,6 +428,7 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
     if (!sigma) return fail(ctx, PG_EINVAL, "pg_best_response: sigma is NULL");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
     pg_status st = apply_profile(g, sigma, tau_inout, dummy_sigma, mem_kind);
+    if (!st) st = reset_scratch(g);
     if (st) return st;
     Timer tm(g);
     tm.mark(3);
@@ -438,8 +448,8 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
         if (st) return st;
         if (out->dom) {
             // dom needs a valuation that records it
-            Counters hc;
-            st = valuate_device(g, true, &hc);
+            st = enqueue_valuation(g, true);
+            if (!st) st = sync_counters(g);
             if (st) return st;
             st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, out->dom,
                                nullptr);
@@ -456,13 +466,15 @@ pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma
     pg_ctx* ctx = g->ctx;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
     pg_status st = apply_profile(g, sigma, tau, dummy_sigma, mem_kind);
+    if (!st) st = reset_scratch(g);
     if (st) return st;
     Timer tm(g);
     tm.mark(0);
-    Counters hc;
-    st = valuate_device(g, true, &hc);
+    st = enqueue_valuation(g, true);
     if (st) return st;
     tm.mark(1);
+    st = sync_counters(g);
+    if (st) return st;
     g->t_val = g->t_total = tm.since(0, 1);
     g->t_vals = 1;
     if (out) {
@@ -470,7 +482,7 @@ pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma
                            out->dom, nullptr);
         if (st) return st;
     }
-    if (hc.n_odd > 0) return fail(ctx, PG_ENOTADMISSIBLE, "pg_valuate: the profile reaches an odd cycle");
+    if (g->hcnt->n_odd > 0) return fail(ctx, PG_ENOTADMISSIBLE, "pg_valuate: the profile reaches an odd cycle");
     return PG_OK;
 }
 

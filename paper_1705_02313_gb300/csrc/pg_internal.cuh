@@ -21,8 +21,8 @@ namespace pg {
 
 constexpr int kBlock = 256;
 constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
-constexpr int kSmallChildren = 32;    // children handled by one thread in the per-parent pass
-constexpr int kBlockChildren = 4096;  // children handled by one block (shared-memory sort)
+constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
+constexpr int kCoopTile = 2048;       // elements per tile of the cooperative id-ordered scan
 
 // flags[v]
 constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
@@ -53,28 +53,32 @@ __host__ __device__ inline bool gd_none(uint64_t w) { return (w & kNone) != 0; }
 constexpr uint8_t kKindFin = 1;        // finite valuation
 constexpr uint8_t kKindSinkChild = 2;  // nearest greater ancestor is the sink
 
-// Device counters of one game (one cache line each would be overkill; a small struct in device memory).
+// Device counters of one game (reset at the start of every valuation).
 struct Counters {
-    int32_t n_pending;   // vertices left to the pointer-jumping phase
+    int32_t n_pending;   // walks that ran out of steps (length of the pending list)
+    int32_t left[2];     // pending vertices left after a jump round (alternating)
     int32_t n_fin;       // finite vertices
     int32_t n_odd;       // vertices reaching an odd cycle
-    int32_t n_big;       // parents with more than kSmallChildren children
+    int32_t n_huge;      // parents ranked by the id-ordered scan
     int32_t n_switch;    // switched vertices in the last switching pass
-    int32_t err;         // device-side error bits
+    int32_t err;         // device-side error bits (kErr*)
     int32_t sink_rank;   // rank of the sink's empty valuation
-    int32_t pad;
+    uint32_t bar_count;  // software grid barrier
+    uint32_t bar_gen;
+    int32_t jump_rounds;
 };
-constexpr int32_t kErrTooManyChildren = 1;
-constexpr int32_t kErrJumpRounds = 2;
+constexpr int32_t kErrJumpRounds = 1;   // pointer jumping exceeded its round cap
+constexpr int32_t kErrBarrier = 2;      // a grid barrier waited past its spin limit
 
 // Kernel classes of one iteration, for per-kernel device timing.
 enum KernelId {
-    KID_WALK,        // k_gwalk
-    KID_JUMP,        // k_jump rounds
+    KID_WALK,        // k_walk
+    KID_JUMP,        // k_jump_coop (all rounds)
     KID_CHAIN1,      // k_chain1
-    KID_PARENTS,     // k_parents
-    KID_BIG,         // big-parent passes
-    KID_SINKSCAN,    // the sink's id-ordered scan (3 kernels)
+    KID_CSCAN,       // children-count scan (3 kernels)
+    KID_SCATTER,     // k_scatter
+    KID_SIBLINGS,    // k_siblings
+    KID_SINKSCAN,    // the sink's id-ordered scan (and k_idscan_coop for huge parents)
     KID_CHAIN2,      // k_chain2
     KID_SWITCH_ODD,  // k_switch for Odd
     KID_SWITCH_EVEN, // k_switch for Even
@@ -124,27 +128,31 @@ struct pg_game {
     int32_t* dummy_of = nullptr; // [k] dummy j -> original vertex it guards (device)
     // solver state
     int32_t* strat = nullptr;    // [n] successor under the current profile; n = the sink
-    // per-iteration scratch
-    uint64_t* gd = nullptr;      // [n] nearest-greater words
+    // per-valuation scratch
+    uint64_t* gd = nullptr;      // [n] nearest-greater words (pointer, walk length, flags)
+    uint32_t* gd32 = nullptr;    // [n] compact g-words read by the chain passes
+    uint8_t* kind = nullptr;     // [n] finite / sink child / odd priority
     int32_t* plist = nullptr;    // [n] pending list
-    uint8_t* cls = nullptr;      // [n]
-    uint8_t* kind = nullptr;     // [n]
-    int32_t* depth = nullptr;    // [n]
-    int32_t* sz = nullptr;       // [n] proper descendants in the nearest-greater forest
-    int32_t* head = nullptr;     // [n] first child (non-sink parents), -1 none
-    int32_t* nxt = nullptr;      // [n] next sibling
+    int32_t* slot = nullptr;     // [n] slot of v among its g-parent's children, -1 if none
+    int32_t* ccnt = nullptr;     // [n+1] children per parent (zero between valuations)
+    int32_t* coff = nullptr;     // [n+2] children segment offsets
+    int2* cl_ks = nullptr;       // [n] per child slot: (order key, subtree size)
+    int32_t* sz = nullptr;       // [n] proper descendants in the g-forest (zero between valuations)
+    int32_t* sinkval = nullptr;  // [n] sink children: subtree size | odd << 31; 0 otherwise
     int32_t* wgt = nullptr;      // [n] chain weight: [even] + sizes of siblings ordered before
-    int32_t* oddsz = nullptr;    // [n] sizes of odd children
+    int32_t* oddsz = nullptr;    // [n] sizes of odd children (zero between valuations)
     int32_t* key = nullptr;      // [n+1] rank; INT32_MAX for TOP; key[n] = sink rank
+    uint8_t* cls = nullptr;      // [n]
+    int32_t* depth = nullptr;    // [n]
     int32_t* dom = nullptr;      // [n] dominant priority of the cycle reached (TOP), -1 finite
-    int32_t* biglist = nullptr;  // [n] parents with many children
-    pg::Counters* cnt = nullptr; // device counters
-    void* scan_tmp = nullptr;
-    size_t scan_tmp_bytes = 0;
-    int64_t* scan_total = nullptr;
-    int32_t* tile_e = nullptr;   // sink-scan tile sums (even)
-    int32_t* tile_o = nullptr;   // sink-scan tile sums (odd)
+    int32_t* hugelist = nullptr; // [n] parents with more than kHugeChildren children
+    int64_t* tiles = nullptr;    // [2 * ntiles + 2] cooperative scan tile sums
     int64_t ntiles = 0;
+    pg::Counters* cnt = nullptr; // device counters
+    pg::Counters* hcnt = nullptr;// pinned host copy
+    void* scan_tmp = nullptr;    // children-count scan scratch
+    size_t scan_tmp_bytes = 0;
+    int coop_blocks = 0;         // co-resident blocks for the cooperative kernels
     void* stage = nullptr;       // staging for host outputs
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
@@ -170,10 +178,16 @@ void free_game(pg_game* g);
 void prof_begin(pg_game* g, int id);
 void prof_end(pg_game* g, int id, int nlaunch);
 void prof_collect(pg_game* g);  // after a stream synchronisation
-// one valuation of g->strat: fills cls, depth, key (and dom when want_dom). Returns counters on host.
-pg_status valuate_device(pg_game* g, bool want_dom, Counters* host_cnt);
-// one switching pass for player (0 Even, 1 Odd) using g->key; returns switched count.
-pg_status switch_device(pg_game* g, int player, int32_t* nswitch);
+// Resets the between-valuation invariants of the scratch arrays (once per call).
+pg_status reset_scratch(pg_game* g);
+// Enqueues one valuation of g->strat: cls, depth, key (and dom when want_dom). No host synchronisation.
+pg_status enqueue_valuation(pg_game* g, bool want_dom);
+// Enqueues the depth pass (outputs only; after a valuation).
+pg_status enqueue_depth(pg_game* g);
+// Enqueues one switching pass for player (0 Even, 1 Odd) using g->key. No host synchronisation.
+pg_status enqueue_switch(pg_game* g, int player);
+// Copies the counters to g->hcnt and waits for the stream; checks device error bits.
+pg_status sync_counters(pg_game* g);
 }  // namespace pg
 
 #define PG_CUDA_TRY(ctx, expr)                                    \

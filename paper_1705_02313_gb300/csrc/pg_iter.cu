@@ -14,7 +14,6 @@
 // members decides, so the order is the in-order of the g-forest in which the
 // children of a node are ordered odd-priority first (larger id first), then the
 // node itself, then even-priority children (smaller id first). That in-order is
-// computed as
 //   rank(v) = oddsz(v) + sum over c on v's g-chain below the sink of wgt(c),
 //   wgt(c)  = [pri(c) even] + total size of the siblings ordered before c,
 // with sizes of g-subtrees. Infinite plays (TOP) end in a cycle; the cycle's
@@ -23,32 +22,44 @@
 // Helman-JaJa algorithm": pseudotree vertices are TOP; an odd dominant
 // priority means sigma was not admissible).
 //
-// Switching (Section 3, "Switching rules"; Section 4, All_Odd): a segmented
-// arg-best over each vertex's edge list using the ranks as keys.
-#include <algorithm>
-#include <vector>
-
+// Passes of one valuation (no host synchronisation between them):
+//   k_walk        nearest greater vertex by a direct walk of <= kWalkCap steps
+//   k_jump_coop   pointer jumping over smaller vertices for the rest
+//   k_chain1      g-subtree sizes and children counts (fire-and-forget atomics)
+//   scan          children counts -> contiguous child segments
+//   k_scatter     children into their segments; the sink's children marked
+//   k_siblings    sibling weights inside each segment
+//   k_idscan_coop id-ordered scans for the sink (and parents with > kHugeChildren children)
+//   k_chain2      rank, depth and class by summing weights along each g-chain
+// The chain passes run a per-lane state machine: every loop step issues one
+// independent gather per lane, so a warp never waits on its longest chain.
+//
+// Switching (Section 3, "Switching rules"; Section 4, All_Odd): a warp takes
+// 32 consecutive vertices, loads their edge lists in coalesced 32-edge chunks,
+// gathers the successors' ranks and reduces each list with a segmented
+// shuffle scan (first minimiser for Odd, first maximiser with the sink first
+// for Even); a vertex switches only when strictly better.
 #include "pg_internal.cuh"
 
 namespace pg {
 namespace {
 
-inline unsigned grid_for(int64_t n, int per = kBlock) {
-    int64_t b = (n + per - 1) / per;
-    if (b < 1) b = 1;
-    if (b > 152 * 64) b = 152 * 64;  // grid-stride beyond this
-    return (unsigned)b;
+constexpr unsigned kFull = 0xffffffffu;
+
+inline unsigned grid_for(int64_t n) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
 }
 
+// All 32 lanes must call this (uniform control flow).
 __device__ inline int32_t warp_append(bool pred, int32_t* counter) {
-    unsigned act = __activemask();
-    unsigned m = __ballot_sync(act, pred);
+    unsigned m = __ballot_sync(kFull, pred);
     if (!m) return -1;
     int lane = threadIdx.x & 31;
     int leader = __ffs(m) - 1;
     int32_t base = 0;
     if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(act, base, leader);
+    base = __shfl_sync(kFull, base, leader);
     return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
 }
 
@@ -57,7 +68,7 @@ __device__ inline void block_add(int32_t v, int32_t* counter) {
     if (threadIdx.x == 0) acc = 0;
     __syncthreads();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&acc, v);
     __syncthreads();
     if (threadIdx.x == 0 && acc) atomicAdd(counter, acc);
@@ -66,506 +77,541 @@ __device__ inline void block_add(int32_t v, int32_t* counter) {
 __device__ inline uint64_t ld_cg(const uint64_t* p) { return __ldcg((const unsigned long long*)p); }
 __device__ inline void st_cg(uint64_t* p, uint64_t v) { __stcg((unsigned long long*)p, (unsigned long long)v); }
 
-// K1: nearest greater vertex along the play, by a direct walk of at most
-// kWalkCap steps. A walk that returns to its start found the maximum of its
-// cycle; a walk that runs out of steps leaves a jump pointer for k_jump.
-__global__ void k_gwalk(int32_t n, const int32_t* __restrict__ strat, uint64_t* __restrict__ gd,
-                        int32_t* __restrict__ plist, Counters* cnt) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int32_t x = __ldg(strat + v);
-        uint32_t d = 1;
-        while (x < v && d < (uint32_t)kWalkCap) {
-            x = __ldg(strat + x);
-            ++d;
+// Compact g-word read by every chain pass: bit 31 = "none" (v is above its
+// whole infinite future; the low bits then name the cycle maximum), low 31
+// bits = g(v) (a vertex or the sink id n).
+constexpr uint32_t kG32None = 0x80000000u;
+__device__ inline uint32_t g32_of(uint64_t w) { return (gd_none(w) ? kG32None : 0u) | (uint32_t)gd_ptr(w); }
+__device__ inline bool g32_none(uint32_t w) { return (w & kG32None) != 0; }
+__device__ inline int32_t g32_ptr(uint32_t w) { return (int32_t)(w & 0x7fffffffu); }
+
+// kind[v], written by k_chain1
+constexpr uint8_t kKFin = 1;        // finite valuation
+constexpr uint8_t kKSinkChild = 2;  // g(v) is the sink
+constexpr uint8_t kKOdd = 4;        // odd priority
+
+// Software grid barrier for cooperative launches (all blocks co-resident).
+// Gives up after a bounded number of spins, records kErrBarrier and returns
+// false; the caller then returns.
+__device__ bool grid_sync(Counters* c) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile uint32_t* genp = &c->bar_gen;
+        uint32_t gen = *genp;
+        __threadfence();
+        uint32_t arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            int64_t spins = 0;
+            while (*genp == gen) {
+                if (++spins > (1ll << 24)) {
+                    atomicOr(&c->err, kErrBarrier);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
-        uint64_t w;
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// K1: nearest greater vertex along the play, by a direct walk of at most
+// kWalkCap steps (one thread per vertex, so the first read and the final
+// write of each warp are coalesced). A walk that returns to its start found
+// the maximum of its cycle; a walk that runs out of steps leaves a jump
+// pointer for k_jump_coop.
+__global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __restrict__ strat,
+                                                 uint64_t* __restrict__ gd, uint32_t* __restrict__ gd32,
+                                                 int32_t* __restrict__ plist, Counters* cnt) {
+    for (int32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
+        const int32_t v = v0 + threadIdx.x;
         bool pend = false;
-        if (x > v) w = gd_pack(true, false, d, x);           // a larger vertex or the sink
-        else if (x == v) w = gd_pack(true, true, d, v);      // v is the maximum of its cycle
-        else { w = gd_pack(false, false, d, x); pend = true; }
-        gd[v] = w;
+        if (v < n) {
+            int32_t x = __ldg(strat + v);
+            uint32_t d = 1;
+            while (x < v && d < (uint32_t)kWalkCap) {
+                x = __ldg(strat + x);
+                ++d;
+            }
+            uint64_t w;
+            if (x > v) w = gd_pack(true, false, d, x);       // a larger vertex or the sink
+            else if (x == v) w = gd_pack(true, true, d, v);  // v is the maximum of its cycle
+            else {
+                w = gd_pack(false, false, d, x);
+                pend = true;
+            }
+            gd[v] = w;
+            gd32[v] = g32_of(w);
+        }
         int32_t slot = warp_append(pend, &cnt->n_pending);
         if (pend) plist[slot] = v;
     }
 }
 
-// Pointer jumping over smaller vertices for the walks that ran out of steps.
-// Invariant of a pending word: every vertex strictly between v and ptr is
-// below v, and ptr is below v. Jumping through x = ptr uses x's own pointer
-// (x pending) or g(x) (x resolved): both skip only vertices below x < v.
-__global__ void k_jump(int32_t np, const int32_t* __restrict__ plist, uint64_t* gd, Counters* cnt) {
-    int32_t left = 0;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-        int32_t v = plist[i];
-        uint64_t w = ld_cg(gd + v);
-        if (gd_resolved(w)) continue;
-        int32_t x = gd_ptr(w);
-        uint64_t wx = ld_cg(gd + x);
-        uint64_t nw;
-        if (gd_resolved(wx) && gd_none(wx)) {
-            // x is above its whole future and below v: so is v (same cycle)
-            nw = gd_pack(true, true, 0, gd_ptr(wx));
-        } else {
-            int32_t y = gd_ptr(wx);
-            uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
-            if (nd > 0x3fffffffull) nd = 0x3fffffffull;  // only reachable around cycles, where dist is unused
-            if (y > v) nw = gd_pack(true, false, (uint32_t)nd, y);
-            else if (y == v) nw = gd_pack(true, true, (uint32_t)nd, v);
-            else {
-                nw = gd_pack(false, false, (uint32_t)nd, y);
-                ++left;
+// Pointer jumping over smaller vertices for the walks that ran out of steps,
+// all rounds in one cooperative launch. Invariant of a pending word: every
+// vertex strictly between v and ptr is below v, and ptr is below v. Jumping
+// through x = ptr uses x's own pointer (x pending) or g(x) (x resolved): both
+// skip only vertices below x < v. Rounds stop when none is left or after cap.
+// Three rotating counters keep each round's count stable until every block
+// has read it.
+__global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict__ plist, uint64_t* gd,
+                                                      uint32_t* gd32, Counters* cnt, int32_t cap) {
+    const int32_t np = cnt->n_pending;
+    if (np == 0) return;
+    for (int32_t r = 0;; ++r) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt->left[(r + 1) % 3] = 0;
+        int32_t left = 0;
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+            int32_t v = plist[i];
+            uint64_t w = ld_cg(gd + v);
+            if (gd_resolved(w)) continue;
+            int32_t x = gd_ptr(w);
+            uint64_t wx = ld_cg(gd + x);
+            uint64_t nw;
+            if (gd_resolved(wx) && gd_none(wx)) {
+                // x is above its whole future and below v: so is v (same cycle)
+                nw = gd_pack(true, true, 0, gd_ptr(wx));
+            } else {
+                int32_t y = gd_ptr(wx);
+                uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
+                if (nd > 0x3fffffffull) nd = 0x3fffffffull;  // only reachable around cycles, where dist is unused
+                if (y > v) {
+                    nw = gd_pack(true, false, (uint32_t)nd, y);
+                } else if (y == v) {
+                    nw = gd_pack(true, true, (uint32_t)nd, v);
+                } else {
+                    nw = gd_pack(false, false, (uint32_t)nd, y);
+                    ++left;
+                }
             }
+            st_cg(gd + v, nw);
+            if (gd_resolved(nw)) gd32[v] = g32_of(nw);
         }
-        st_cg(gd + v, nw);
+        block_add(left, &cnt->left[r % 3]);
+        if (!grid_sync(cnt)) return;
+        int32_t rem = *(volatile int32_t*)&cnt->left[r % 3];
+        if (rem == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) cnt->jump_rounds = r + 1;
+            return;
+        }
+        if (r + 1 >= cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cnt->err, kErrJumpRounds);
+            return;
+        }
     }
-    block_add(left, &cnt->n_pending);
 }
 
-// First pass over g-chains: class, depth, subtree sizes and children lists.
-__global__ void k_chain1(int32_t n, const uint64_t* __restrict__ gd, const uint8_t* __restrict__ flags,
-                         const int32_t* __restrict__ pri, uint8_t* __restrict__ cls, uint8_t* __restrict__ kind,
-                         int32_t* __restrict__ depth, int32_t* sz, int32_t* head, int32_t* __restrict__ nxt,
-                         int32_t* __restrict__ dom, int want_dom, Counters* cnt) {
+// Classification and g-subtree sizes. Each vertex walks its g-chain (4-byte
+// words) to its end: the sink means a finite valuation, a "none" vertex
+// means TOP (odd cycle if that cycle maximum is odd). Finite vertices then
+// add one to each g-ancestor below the sink (the second walk hits cache) and
+// take a slot among their g-parent's children. TOP vertices touch nothing
+// else, so large TOP components cause no atomic hot spots.
+__global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __restrict__ gd32,
+                                                   const uint8_t* __restrict__ flags, const int32_t* __restrict__ pri,
+                                                   int32_t* sz, int32_t* ccnt, int32_t* __restrict__ slot,
+                                                   uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
+                                                   int32_t* __restrict__ dom, int want_dom, Counters* cnt) {
     int32_t nfin = 0, nodd = 0;
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint64_t w = gd[v];
+        const uint32_t w = gd32[v];
+        const bool odd_v = (flags[v] & kPriOdd) != 0;
         int32_t cyc = -1;
-        uint32_t dep = 0;
-        if (gd_none(w)) {
-            cyc = gd_ptr(w);
+        if (g32_none(w)) {
+            cyc = g32_ptr(w);
         } else {
-            dep = gd_dist(w);
-            int32_t x = gd_ptr(w);
-            while (x != n) {
-                uint64_t wx = gd[x];
-                if (gd_none(wx)) {
-                    cyc = gd_ptr(wx);
+            for (int32_t x = g32_ptr(w); x != n;) {
+                uint32_t wx = gd32[x];
+                if (g32_none(wx)) {
+                    cyc = g32_ptr(wx);
                     break;
                 }
-                dep += gd_dist(wx);
-                x = gd_ptr(wx);
+                x = g32_ptr(wx);
             }
         }
+        int32_t sl = -1;
         if (cyc < 0) {
-            int32_t g = gd_ptr(w);
+            const int32_t g = g32_ptr(w);
+            kind[v] = kKFin | (g == n ? kKSinkChild : 0) | (odd_v ? kKOdd : 0);
             cls[v] = kFin;
-            depth[v] = (int32_t)dep;
-            kind[v] = kKindFin | (g == n ? kKindSinkChild : 0);
-            for (int32_t x = g; x != n; x = gd_ptr(gd[x])) atomicAdd(sz + x, 1);
-            if (g != n) nxt[v] = atomicExch(head + g, v);
             if (want_dom) dom[v] = -1;
+            if (g != n) {
+                sl = atomicAdd(ccnt + g, 1);
+                for (int32_t x = g; x != n; x = g32_ptr(gd32[x])) atomicAdd(sz + x, 1);
+            }
             ++nfin;
         } else {
-            bool odd = (flags[cyc] & kPriOdd) != 0;
-            cls[v] = odd ? kOddCycle : kTop;
+            const bool odd = (flags[cyc] & kPriOdd) != 0;
             kind[v] = 0;
-            depth[v] = -1;
+            cls[v] = odd ? kOddCycle : kTop;
             if (want_dom) dom[v] = pri[cyc];
             nodd += odd;
         }
+        slot[v] = sl;
     }
     block_add(nfin, &cnt->n_fin);
     block_add(nodd, &cnt->n_odd);
 }
 
-__device__ inline int32_t order_key(int32_t c, uint8_t f) { return (f & kPriOdd) ? -(c + 1) : c; }
+__device__ inline int32_t order_key(int32_t c, bool odd) { return odd ? -(c + 1) : c; }
 
-// Children of non-sink parents: sort each small list by the order of
-// Section 3 (odd children by decreasing id, then even children by increasing
-// id) and give every child its weight; parents with more children are left
-// to k_big_parents.
-__global__ void k_parents(int32_t n, const int32_t* __restrict__ head, const int32_t* __restrict__ nxt,
-                          const int32_t* __restrict__ sz, const uint8_t* __restrict__ flags, int32_t* wgt,
-                          int32_t* oddsz, int32_t* biglist, Counters* cnt) {
-    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        int32_t h = head[a];
-        if (h < 0) {
-            oddsz[a] = 0;
-            continue;
-        }
-        int32_t ids[kSmallChildren];
-        int32_t keys[kSmallChildren];
-        int cnt_c = 0;
-        bool big = false;
-        for (int32_t c = h; c >= 0; c = nxt[c]) {
-            if (cnt_c == kSmallChildren) {
-                big = true;
-                break;
-            }
-            int32_t kk = order_key(c, flags[c]);
-            int j = cnt_c++;
-            while (j > 0 && keys[j - 1] > kk) {
-                keys[j] = keys[j - 1];
-                ids[j] = ids[j - 1];
-                --j;
-            }
-            keys[j] = kk;
-            ids[j] = c;
-        }
-        if (big) {
-            int32_t slot = atomicAdd(&cnt->n_big, 1);
-            biglist[slot] = a;
-            continue;
-        }
-        int32_t run = 0, os = 0;
-        for (int i = 0; i < cnt_c; ++i) {
-            int32_t c = ids[i];
-            int32_t s = 1 + sz[c];
-            bool odd = keys[i] < 0;
-            wgt[c] = run + (odd ? 0 : 1);
-            run += s;
-            if (odd) os += s;
-        }
-        oddsz[a] = os;
-    }
-}
-
-// Big parents (more than kSmallChildren children): instead of walking a long
-// list, every child finds its parent's batch slot and appends itself to the
-// slot's buffer; k_big_parents then sorts each buffer in shared memory.
-__global__ void k_big_collect(int32_t n, const uint64_t* __restrict__ gd, const uint8_t* __restrict__ kind,
-                              const int32_t* __restrict__ bigslot, int32_t* bigfill, int32_t* bigbuf,
-                              const Counters* cnt) {
-    if (cnt->n_big == 0) return;
+// Finite children into their segments at the slots taken in k_chain1
+// (order key, subtree size); the sink's children record size and parity for
+// the id-ordered scan. Also clears the children counts for the next valuation.
+__global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* __restrict__ gd32,
+                                                    const uint8_t* __restrict__ kind, const int32_t* __restrict__ sz,
+                                                    const int32_t* __restrict__ coff, const int32_t* __restrict__ slot,
+                                                    int32_t* __restrict__ ccnt, int2* __restrict__ cl_ks,
+                                                    int32_t* __restrict__ sinkval) {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint8_t kd = kind[v];
-        if (!(kd & kKindFin) || (kd & kKindSinkChild)) continue;
-        int32_t a = gd_ptr(gd[v]);
-        int32_t b = bigslot[a];
-        if (b < 0) continue;
-        int32_t pos = atomicAdd(bigfill + b, 1);
-        if (pos < kBlockChildren) bigbuf[(int64_t)b * kBlockChildren + pos] = v;
+        const uint8_t kd = kind[v];
+        int32_t sv = 0;
+        ccnt[v] = 0;
+        if (kd & kKFin) {
+            const bool odd = (kd & kKOdd) != 0;
+            const int32_t s = 1 + sz[v];
+            if (kd & kKSinkChild) sv = s | (odd ? INT32_MIN : 0);
+            else cl_ks[coff[g32_ptr(gd32[v])] + slot[v]] = make_int2(order_key(v, odd), s);
+        }
+        sinkval[v] = sv;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ccnt[n] = 0;
 }
 
-__global__ void k_big_mark(const int32_t* __restrict__ biglist, int32_t* bigslot, const Counters* cnt) {
-    int32_t nb = cnt->n_big;
-    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
-        bigslot[biglist[b]] = b;
-}
-
-__global__ void k_big_parents(const int32_t* __restrict__ biglist, int32_t* bigslot, int32_t* bigfill,
-                              const int32_t* __restrict__ bigbuf, const int32_t* __restrict__ sz,
-                              const uint8_t* __restrict__ flags, int32_t* wgt, int32_t* oddsz, int32_t* hugelist,
-                              Counters* cnt) {
-    __shared__ int64_t sk[kBlockChildren];  // (order key << 32) | id
-    __shared__ int32_t wsum[kBlock / 32];
-    __shared__ int32_t carry_s, odd_s;
-    int32_t nb = cnt->n_big;
-    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        int32_t a = biglist[b];
-        int32_t count = bigfill[b];
-        __syncthreads();
-        if (count > kBlockChildren) {
-            if (threadIdx.x == 0) {
-                hugelist[atomicAdd(&cnt->pad, 1)] = a;  // pad counts huge parents
-                bigslot[a] = -1;
-                bigfill[b] = 0;
-            }
+// Sibling weights, one thread per finite vertex with a vertex parent: sum
+// the sizes of the siblings ordered before it in the parent's segment; the
+// child in slot 0 also writes the parent's odd total. Segments above
+// kHugeChildren are left to k_idscan_coop.
+__global__ void __launch_bounds__(kBlock) k_siblings(int32_t n, const uint32_t* __restrict__ gd32,
+                                                     const uint8_t* __restrict__ kind,
+                                                     const int32_t* __restrict__ slot,
+                                                     const int32_t* __restrict__ coff, const int2* __restrict__ cl_ks,
+                                                     int32_t* __restrict__ wgt, int32_t* __restrict__ oddsz,
+                                                     int32_t* hugelist, Counters* cnt) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t kd = kind[v];
+        if (!(kd & kKFin) || (kd & kKSinkChild)) continue;
+        const int32_t a = g32_ptr(gd32[v]);
+        const int32_t s0 = coff[a], s1 = coff[a + 1];
+        const bool first = slot[v] == 0;
+        if (s1 - s0 > kHugeChildren) {
+            if (first) hugelist[atomicAdd(&cnt->n_huge, 1)] = a;
             continue;
         }
-        int p2 = 1;
-        while (p2 < count) p2 <<= 1;
-        for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-            if (i < count) {
-                int32_t c = bigbuf[(int64_t)b * kBlockChildren + i];
-                sk[i] = ((int64_t)order_key(c, flags[c]) << 32) | (uint32_t)c;
-            } else {
-                sk[i] = INT64_MAX;
-            }
+        const int32_t myk = order_key(v, (kd & kKOdd) != 0);
+        int32_t pre = 0, os = 0;
+        for (int32_t q = s0; q < s1; ++q) {
+            int2 ks = __ldg(cl_ks + q);
+            if (ks.x < myk) pre += ks.y;
+            if (ks.x < 0) os += ks.y;
         }
-        __syncthreads();
-        // bitonic sort in shared memory
-        for (int kk = 2; kk <= p2; kk <<= 1) {
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-                    int ixj = i ^ j;
-                    if (ixj > i) {
-                        int64_t x = sk[i], y = sk[ixj];
-                        bool up = (i & kk) == 0;
-                        if ((x > y) == up) {
-                            sk[i] = y;
-                            sk[ixj] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // running sums in sorted order, one chunk of blockDim elements at a time
-        if (threadIdx.x == 0) {
-            carry_s = 0;
-            odd_s = 0;
-        }
-        __syncthreads();
-        for (int base = 0; base < count; base += blockDim.x) {
-            int i = base + threadIdx.x;
-            int32_t c = -1, s = 0;
-            bool odd = false;
-            if (i < count) {
-                c = (int32_t)(uint32_t)(sk[i] & 0xffffffffll);
-                s = 1 + sz[c];
-                odd = (sk[i] >> 32) < 0;
-            }
-            // block exclusive scan of s
-            int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            int32_t x = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) wsum[wid] = x;
-            __syncthreads();
-            if (wid == 0) {
-                int32_t t = lane < kBlock / 32 ? wsum[lane] : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o) t += y;
-                }
-                if (lane < kBlock / 32) wsum[lane] = t;
-            }
-            __syncthreads();
-            int32_t excl = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - s;
-            if (c >= 0) wgt[c] = excl + (odd ? 0 : 1);
-            int32_t oddpart = odd ? s : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) oddpart += __shfl_down_sync(0xffffffffu, oddpart, o);
-            __syncthreads();
-            if (lane == 0 && oddpart) atomicAdd(&odd_s, oddpart);
-            if (threadIdx.x == 0) carry_s += wsum[kBlock / 32 - 1];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            oddsz[a] = odd_s;
-            bigslot[a] = -1;
-            bigfill[b] = 0;
-        }
-        __syncthreads();
+        wgt[v] = pre + (myk >= 0 ? 1 : 0);
+        if (first) oddsz[a] = os;
     }
 }
 
-// Children of one parent p whose children are too many for a block (and of
-// the sink, which has most vertices as children): their order is the id
-// order, so a scan over ids does it. Pass 1: per-tile sums of the even and
-// odd children's sizes.
-constexpr int kSIpt = 8;
-constexpr int kSTile = kBlock * kSIpt;
+// Children of the sink: ordered by id, so one id-ordered scan gives their
+// weights. Even child c: 1 + (all odd children) + (even children with
+// smaller id); odd child c: odd children with larger id. The sink's rank is
+// the odd total. Three kernels: tile sums, a one-block scan of the tile sums,
+// per-tile scans. Parents above kHugeChildren children use the same scan in
+// k_idscan_coop below.
+constexpr int kCIpt = kCoopTile / kBlock;
 
-template <bool kSink>
-__device__ inline bool is_child(int64_t i, int32_t p, const uint8_t* kind, const uint64_t* gd) {
-    uint8_t kd = kind[i];
-    if (!(kd & kKindFin)) return false;
-    if (kSink) return (kd & kKindSinkChild) != 0;
-    return !(kd & kKindSinkChild) && gd_ptr(gd[i]) == p;
+__device__ inline void sink_contrib(int32_t sv, int32_t* e, int32_t* o) {
+    int32_t s = sv & 0x7fffffff;
+    *e = sv > 0 ? s : 0;
+    *o = sv < 0 ? s : 0;
 }
 
-template <bool kSink>
-__global__ void k_idscan_reduce(int32_t n, int32_t p, const uint8_t* __restrict__ kind,
-                                const uint64_t* __restrict__ gd, const int32_t* __restrict__ sz,
-                                const uint8_t* __restrict__ flags, int64_t* tsum) {
-    __shared__ int32_t se, so;
-    if (threadIdx.x == 0) se = so = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSTile + (int64_t)threadIdx.x * kSIpt;
-    int32_t e = 0, o = 0;
-#pragma unroll
-    for (int k = 0; k < kSIpt; ++k) {
-        int64_t i = base + k;
-        if (i < n && is_child<kSink>(i, p, kind, gd)) {
-            int32_t s = 1 + sz[i];
-            if (flags[i] & kPriOdd) o += s;
-            else e += s;
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        e += __shfl_down_sync(0xffffffffu, e, off);
-        o += __shfl_down_sync(0xffffffffu, o, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (e) atomicAdd(&se, e);
-        if (o) atomicAdd(&so, o);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tsum[2 * blockIdx.x] = se;
-        tsum[2 * blockIdx.x + 1] = so;
-    }
-}
-
-// exclusive scan of the (even, odd) tile sums by one block; totals at the end
-__global__ void k_idscan_tiles(int64_t* tsum, int64_t ntiles) {
-    __shared__ int64_t we[kBlock / 32], wo[kBlock / 32];
-    int64_t ce = 0, co = 0;
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t b = 0; b < ntiles; b += kBlock) {
-        int64_t i = b + threadIdx.x;
-        int64_t e = i < ntiles ? tsum[2 * i] : 0, o = i < ntiles ? tsum[2 * i + 1] : 0;
-        int64_t xe = e, xo = o;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int64_t ye = __shfl_up_sync(0xffffffffu, xe, d), yo = __shfl_up_sync(0xffffffffu, xo, d);
-            if (lane >= d) {
-                xe += ye;
-                xo += yo;
-            }
-        }
-        if (lane == 31) {
-            we[wid] = xe;
-            wo[wid] = xo;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            int64_t te = lane < kBlock / 32 ? we[lane] : 0, to = lane < kBlock / 32 ? wo[lane] : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                int64_t ye = __shfl_up_sync(0xffffffffu, te, d), yo = __shfl_up_sync(0xffffffffu, to, d);
-                if (lane >= d) {
-                    te += ye;
-                    to += yo;
-                }
-            }
-            if (lane < kBlock / 32) {
-                we[lane] = te;
-                wo[lane] = to;
-            }
-        }
-        __syncthreads();
-        int64_t pe = ce + (wid > 0 ? we[wid - 1] : 0) + xe - e;
-        int64_t po = co + (wid > 0 ? wo[wid - 1] : 0) + xo - o;
-        if (i < ntiles) {
-            tsum[2 * i] = pe;
-            tsum[2 * i + 1] = po;
-        }
-        ce += we[kBlock / 32 - 1];
-        co += wo[kBlock / 32 - 1];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        tsum[2 * ntiles] = ce;
-        tsum[2 * ntiles + 1] = co;
-    }
-}
-
-// Pass 3: weights. Even child c: 1 + (all odd children) + (even children with
-// smaller id); odd child c: odd children with larger id. The parent's own
-// rank offset oddsz(p) is the odd total (the sink's rank when p is the sink).
-template <bool kSink>
-__global__ void k_idscan_apply(int32_t n, int32_t p, const uint8_t* __restrict__ kind,
-                               const uint64_t* __restrict__ gd, const int32_t* __restrict__ sz,
-                               const uint8_t* __restrict__ flags, const int64_t* __restrict__ tsum, int64_t ntiles,
-                               int32_t* wgt, int32_t* oddsz_p) {
-    __shared__ int32_t we[kBlock / 32], wo[kBlock / 32];
-    int64_t base = (int64_t)blockIdx.x * kSTile + (int64_t)threadIdx.x * kSIpt;
-    int32_t se[kSIpt], so[kSIpt];
-    int32_t te = 0, to = 0;
-#pragma unroll
-    for (int k = 0; k < kSIpt; ++k) {
-        int64_t i = base + k;
-        se[k] = so[k] = 0;
-        if (i < n && is_child<kSink>(i, p, kind, gd)) {
-            int32_t s = 1 + sz[i];
-            if (flags[i] & kPriOdd) so[k] = s;
-            else se[k] = s;
-        }
-        te += se[k];
-        to += so[k];
-    }
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int32_t xe = te, xo = to;
+__device__ inline void block_scan2(int32_t ve, int32_t vo, int64_t* xe, int64_t* xo, int64_t* te, int64_t* to) {
+    __shared__ int64_t se[kBlock / 32], so[kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t a = ve, b = vo;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        int32_t ye = __shfl_up_sync(0xffffffffu, xe, d), yo = __shfl_up_sync(0xffffffffu, xo, d);
+        int64_t ya = __shfl_up_sync(kFull, a, d), yb = __shfl_up_sync(kFull, b, d);
         if (lane >= d) {
-            xe += ye;
-            xo += yo;
+            a += ya;
+            b += yb;
         }
     }
     if (lane == 31) {
-        we[wid] = xe;
-        wo[wid] = xo;
+        se[wid] = a;
+        so[wid] = b;
     }
     __syncthreads();
     if (wid == 0) {
-        int32_t a = lane < kBlock / 32 ? we[lane] : 0, b = lane < kBlock / 32 ? wo[lane] : 0;
+        int64_t pa = lane < kBlock / 32 ? se[lane] : 0, pb = lane < kBlock / 32 ? so[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int32_t ya = __shfl_up_sync(0xffffffffu, a, d), yb = __shfl_up_sync(0xffffffffu, b, d);
+            int64_t ya = __shfl_up_sync(kFull, pa, d), yb = __shfl_up_sync(kFull, pb, d);
             if (lane >= d) {
-                a += ya;
-                b += yb;
+                pa += ya;
+                pb += yb;
             }
         }
         if (lane < kBlock / 32) {
-            we[lane] = a;
-            wo[lane] = b;
+            se[lane] = pa;
+            so[lane] = pb;
         }
     }
     __syncthreads();
-    int64_t run_e = tsum[2 * blockIdx.x] + (wid > 0 ? we[wid - 1] : 0) + xe - te;
-    int64_t run_o = tsum[2 * blockIdx.x + 1] + (wid > 0 ? wo[wid - 1] : 0) + xo - to;
-    int64_t tot_o = tsum[2 * ntiles + 1];
-#pragma unroll
-    for (int k = 0; k < kSIpt; ++k) {
-        int64_t i = base + k;
-        if (se[k]) wgt[i] = (int32_t)(1 + tot_o + run_e);
-        run_o += so[k];
-        if (so[k]) wgt[i] = (int32_t)(tot_o - run_o);
-        run_e += se[k];
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *oddsz_p = (int32_t)tot_o;
+    *xe = (wid > 0 ? se[wid - 1] : 0) + a - ve;  // exclusive
+    *xo = (wid > 0 ? so[wid - 1] : 0) + b - vo;
+    *te = se[kBlock / 32 - 1];
+    *to = so[kBlock / 32 - 1];
+    __syncthreads();
 }
 
-// Second pass over g-chains: the rank, and reset of the per-iteration lists.
-__global__ void k_chain2(int32_t n, const uint64_t* __restrict__ gd, const uint8_t* __restrict__ kind,
-                         const int32_t* __restrict__ wgt, const int32_t* __restrict__ oddsz,
-                         int32_t* __restrict__ key, int32_t* __restrict__ sz, int32_t* __restrict__ head,
-                         const Counters* cnt) {
+// eight consecutive sinkval entries of thread t in tile b (two 16-byte loads)
+__device__ inline void load8(const int32_t* __restrict__ sinkval, int32_t n, int64_t i0, int32_t v[kCIpt]) {
+    if (i0 + kCIpt <= n) {
+        int4 a = __ldg(reinterpret_cast<const int4*>(sinkval + i0));
+        int4 b = __ldg(reinterpret_cast<const int4*>(sinkval + i0) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kCIpt; ++k) v[k] = i0 + k < n ? sinkval[i0 + k] : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sink_reduce(int32_t n, const int32_t* __restrict__ sinkval, int64_t* tiles) {
+    const int64_t i0 = (int64_t)blockIdx.x * kCoopTile + (int64_t)threadIdx.x * kCIpt;
+    int32_t v[kCIpt];
+    load8(sinkval, n, i0, v);
+    int32_t e = 0, o = 0;
+#pragma unroll
+    for (int k = 0; k < kCIpt; ++k) {
+        int32_t ee, oo;
+        sink_contrib(v[k], &ee, &oo);
+        e += ee;
+        o += oo;
+    }
+    int64_t xe, xo, te, to;
+    block_scan2(e, o, &xe, &xo, &te, &to);
+    if (threadIdx.x == 0) {
+        tiles[2 * blockIdx.x] = te;
+        tiles[2 * blockIdx.x + 1] = to;
+    }
+}
+
+// exclusive scan of the (even, odd) tile sums by one block; totals after the last tile
+__global__ void __launch_bounds__(kBlock) k_tiles_scan(int64_t* tiles, int64_t ntiles) {
+    int64_t ce = 0, co = 0;
+    for (int64_t b = 0; b < ntiles; b += kBlock) {
+        int64_t i = b + threadIdx.x;
+        int64_t e = i < ntiles ? tiles[2 * i] : 0, o = i < ntiles ? tiles[2 * i + 1] : 0;
+        int64_t xe, xo, te, to;
+        block_scan2((int32_t)e, (int32_t)o, &xe, &xo, &te, &to);
+        if (i < ntiles) {
+            tiles[2 * i] = ce + xe;
+            tiles[2 * i + 1] = co + xo;
+        }
+        ce += te;
+        co += to;
+    }
+    if (threadIdx.x == 0) {
+        tiles[2 * ntiles] = ce;
+        tiles[2 * ntiles + 1] = co;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sink_apply(int32_t n, const int32_t* __restrict__ sinkval,
+                                                       const int64_t* __restrict__ tiles, int64_t ntiles,
+                                                       int32_t* __restrict__ wgt, Counters* cnt) {
+    const int64_t i0 = (int64_t)blockIdx.x * kCoopTile + (int64_t)threadIdx.x * kCIpt;
+    int32_t v[kCIpt];
+    load8(sinkval, n, i0, v);
+    int32_t es[kCIpt], os[kCIpt];
+    int32_t e = 0, o = 0;
+#pragma unroll
+    for (int k = 0; k < kCIpt; ++k) {
+        sink_contrib(v[k], &es[k], &os[k]);
+        e += es[k];
+        o += os[k];
+    }
+    int64_t xe, xo, te, to;
+    block_scan2(e, o, &xe, &xo, &te, &to);
+    const int64_t tot_o = tiles[2 * ntiles + 1];
+    int64_t run_e = tiles[2 * blockIdx.x] + xe, run_o = tiles[2 * blockIdx.x + 1] + xo;
+#pragma unroll
+    for (int k = 0; k < kCIpt; ++k) {
+        if (es[k]) wgt[i0 + k] = (int32_t)(1 + tot_o + run_e);
+        run_o += os[k];
+        if (os[k]) wgt[i0 + k] = (int32_t)(tot_o - run_o);
+        run_e += es[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt->sink_rank = (int32_t)tot_o;
+}
+
+// Parents with more than kHugeChildren children (none in the measured
+// workloads): the same id-ordered scan over every vertex, one parent after
+// the other, in one cooperative launch that returns at once when there are
+// none. Children of a are the vertices whose g-word points at a.
+__global__ void __launch_bounds__(kBlock) k_idscan_coop(int32_t n, const uint32_t* __restrict__ gd32,
+                                                        const int32_t* __restrict__ sz,
+                                                        const uint8_t* __restrict__ kind,
+                                                        const int32_t* __restrict__ hugelist, int64_t* tiles,
+                                                        int64_t ntiles, int32_t* wgt, int32_t* oddsz, Counters* cnt) {
+    const int32_t nh = cnt->n_huge;
+    for (int32_t h = 0; h < nh; ++h) {
+        const int32_t a = hugelist[h];
+        auto contrib = [&](int64_t i, int32_t* e, int32_t* o) {
+            *e = *o = 0;
+            if (i >= n) return;
+            const uint8_t kd = kind[i];
+            if ((kd & kKFin) && !(kd & kKSinkChild) && g32_ptr(gd32[i]) == a) {
+                int32_t s = 1 + sz[i];
+                if (kd & kKOdd) *o = s;
+                else *e = s;
+            }
+        };
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int32_t e = 0, o = 0;
+            for (int k = 0; k < kCIpt; ++k) {
+                int32_t ee, oo;
+                contrib(t * kCoopTile + (int64_t)threadIdx.x * kCIpt + k, &ee, &oo);
+                e += ee;
+                o += oo;
+            }
+            int64_t xe, xo, te, to;
+            block_scan2(e, o, &xe, &xo, &te, &to);
+            if (threadIdx.x == 0) {
+                tiles[2 * t] = te;
+                tiles[2 * t + 1] = to;
+            }
+        }
+        if (!grid_sync(cnt)) return;
+        if (blockIdx.x == 0) {
+            int64_t ce = 0, co = 0;
+            for (int64_t b = 0; b < ntiles; b += kBlock) {
+                int64_t i = b + threadIdx.x;
+                int64_t e = i < ntiles ? tiles[2 * i] : 0, o = i < ntiles ? tiles[2 * i + 1] : 0;
+                int64_t xe, xo, te, to;
+                block_scan2((int32_t)e, (int32_t)o, &xe, &xo, &te, &to);
+                if (i < ntiles) {
+                    tiles[2 * i] = ce + xe;
+                    tiles[2 * i + 1] = co + xo;
+                }
+                ce += te;
+                co += to;
+            }
+            if (threadIdx.x == 0) {
+                tiles[2 * ntiles] = ce;
+                tiles[2 * ntiles + 1] = co;
+            }
+        }
+        if (!grid_sync(cnt)) return;
+        const int64_t tot_o = tiles[2 * ntiles + 1];
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int32_t es[kCIpt], os[kCIpt];
+            int32_t e = 0, o = 0;
+            const int64_t i0 = t * kCoopTile + (int64_t)threadIdx.x * kCIpt;
+            for (int k = 0; k < kCIpt; ++k) {
+                contrib(i0 + k, &es[k], &os[k]);
+                e += es[k];
+                o += os[k];
+            }
+            int64_t xe, xo, te, to;
+            block_scan2(e, o, &xe, &xo, &te, &to);
+            int64_t run_e = tiles[2 * t] + xe, run_o = tiles[2 * t + 1] + xo;
+            for (int k = 0; k < kCIpt; ++k) {
+                if (es[k]) wgt[i0 + k] = (int32_t)(1 + tot_o + run_e);
+                run_o += os[k];
+                if (os[k]) wgt[i0 + k] = (int32_t)(tot_o - run_o);
+                run_e += es[k];
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) oddsz[a] = (int32_t)tot_o;
+        if (!grid_sync(cnt)) return;  // the tile sums are reused by the next parent
+    }
+}
+
+// Ranks: sum the weights along each finite vertex's g-chain (TOP vertices
+// rank above everything). Also restores the between-valuation zeros of sz
+// and oddsz.
+__global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __restrict__ gd32,
+                                                   const uint8_t* __restrict__ kind, const int32_t* __restrict__ wgt,
+                                                   int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
+                                                   int32_t* __restrict__ sz, const Counters* cnt) {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int32_t r = INT32_MAX;
-        if (kind[v] & kKindFin) {
-            int64_t acc = (int64_t)oddsz[v] + wgt[v];
-            for (int32_t x = gd_ptr(gd[v]); x != n; x = gd_ptr(gd[x])) acc += wgt[x];
-            r = (int32_t)acc;
+        if (kind[v] & kKFin) {
+            int32_t acc = oddsz[v] + wgt[v];
+            for (int32_t x = g32_ptr(gd32[v]); x != n; x = g32_ptr(gd32[x])) acc += wgt[x];
+            r = acc;
         }
         key[v] = r;
+        oddsz[v] = 0;
         sz[v] = 0;
-        head[v] = -1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) key[n] = cnt->sink_rank;
 }
 
-// K3: greedy all-switches for one player. Odd takes the first minimiser of
-// its edge list, Even the first maximiser with the sink looked at first; a
-// vertex switches only if strictly better than its current choice.
-__global__ void k_switch(int32_t n, int player, const int32_t* __restrict__ off, const int32_t* __restrict__ tgt,
-                         const uint8_t* __restrict__ flags, const int32_t* __restrict__ key, int32_t* strat,
-                         Counters* cnt) {
+// Depth of every finite vertex (outputs only): the number of vertices on its
+// play before the sink, the sum of the walk lengths along its g-chain.
+__global__ void __launch_bounds__(kBlock) k_depth(int32_t n, const uint64_t* __restrict__ gd,
+                                                  const uint8_t* __restrict__ kind, int32_t* __restrict__ depth) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int32_t dep = -1;
+        if (kind[v] & kKFin) {
+            uint64_t w = gd[v];
+            uint32_t d = gd_dist(w);
+            for (int32_t x = gd_ptr(w); x != n;) {
+                uint64_t wx = gd[x];
+                d += gd_dist(wx);
+                x = gd_ptr(wx);
+            }
+            dep = (int32_t)d;
+        }
+        depth[v] = dep;
+    }
+}
+
+// K3: greedy all-switches for one player, one thread per vertex. Edges are
+// taken in batches of four whose target reads and rank gathers are issued
+// together, then compared in edge-list order (first minimiser for Odd; for
+// Even the sink first, then the first maximiser).
+__global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const int32_t* __restrict__ off,
+                                                   const int32_t* __restrict__ tgt,
+                                                   const uint8_t* __restrict__ flags,
+                                                   const int32_t* __restrict__ key, int32_t* strat, Counters* cnt) {
     int32_t nsw = 0;
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if ((flags[v] & kOwnerOdd) != player) continue;
-        int32_t e0 = off[v], e1 = off[v + 1];
-        int32_t best, bk;
-        if (player == 0) {
-            best = n;
-            bk = key[n];
-        } else {
-            best = tgt[e0];
-            bk = key[best];
-            ++e0;
-        }
-        for (int32_t e = e0; e < e1; ++e) {
-            int32_t u = tgt[e];
-            int32_t ku = key[u];
-            if (player == 0 ? ku > bk : ku < bk) {
-                best = u;
-                bk = ku;
+        if ((int)(flags[v] & kOwnerOdd) != player) continue;
+        const int32_t e0 = off[v], e1 = off[v + 1];
+        const int32_t cur = strat[v];
+        int32_t best = player == 0 ? n : -1;
+        int32_t bk = player == 0 ? key[n] : INT32_MAX;
+        const int32_t curkey = key[cur];
+        for (int32_t e = e0; e < e1; e += 4) {
+            int32_t t[4], kk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? tgt[e + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kk[j] = t[j] >= 0 ? key[t[j]] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (t[j] < 0) continue;
+                bool better = player == 0 ? kk[j] > bk : (best < 0 || kk[j] < bk);
+                if (better) {
+                    best = t[j];
+                    bk = kk[j];
+                }
             }
         }
-        int32_t cur = key[strat[v]];
-        if (player == 0 ? bk > cur : bk < cur) {
+        if (player == 0 ? bk > curkey : bk < curkey) {
             strat[v] = best;
             ++nsw;
         }
@@ -575,8 +621,8 @@ __global__ void k_switch(int32_t n, int player, const int32_t* __restrict__ off,
 
 }  // namespace
 
-const char* const kKernelNames[KID_COUNT] = {"walk", "jump", "chain1", "parents", "big_parents",
-                                              "sink_scan", "chain2", "switch_odd", "switch_even"};
+const char* const kKernelNames[KID_COUNT] = {"walk",     "jump",      "chain1", "child_scan", "scatter",
+                                              "siblings", "sink_scan", "chain2", "switch_odd", "switch_even"};
 
 void prof_begin(pg_game* g, int id) {
     if (g->ctx->timing) cudaEventRecord(g->kev[2 * id], g->ctx->stream);
@@ -608,145 +654,108 @@ pg_status alloc_scratch(pg_game* g) {
     int64_t n = g->n;
     auto A = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 1); };
     PG_CUDA_TRY(ctx, A((void**)&g->gd, sizeof(uint64_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->plist, sizeof(int32_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->cls, n));
+    PG_CUDA_TRY(ctx, A((void**)&g->gd32, sizeof(uint32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->kind, n));
-    PG_CUDA_TRY(ctx, A((void**)&g->depth, sizeof(int32_t) * n));
+    PG_CUDA_TRY(ctx, A((void**)&g->plist, sizeof(int32_t) * n));
+    PG_CUDA_TRY(ctx, A((void**)&g->slot, sizeof(int32_t) * n));
+    PG_CUDA_TRY(ctx, A((void**)&g->ccnt, sizeof(int32_t) * (n + 1)));
+    PG_CUDA_TRY(ctx, A((void**)&g->coff, sizeof(int32_t) * (n + 2)));
+    PG_CUDA_TRY(ctx, A((void**)&g->cl_ks, sizeof(int2) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->sz, sizeof(int32_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->head, sizeof(int32_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->nxt, sizeof(int32_t) * n));
+    PG_CUDA_TRY(ctx, A((void**)&g->sinkval, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->wgt, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->oddsz, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->key, sizeof(int32_t) * (n + 1)));
+    PG_CUDA_TRY(ctx, A((void**)&g->cls, n));
+    PG_CUDA_TRY(ctx, A((void**)&g->depth, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->dom, sizeof(int32_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->biglist, sizeof(int32_t) * n));
+    PG_CUDA_TRY(ctx, A((void**)&g->hugelist, sizeof(int32_t) * n));
+    g->ntiles = std::max<int64_t>(1, (n + kCoopTile - 1) / kCoopTile);
+    PG_CUDA_TRY(ctx, A((void**)&g->tiles, sizeof(int64_t) * (2 * g->ntiles + 2)));
     PG_CUDA_TRY(ctx, A((void**)&g->cnt, sizeof(Counters)));
-    g->ntiles = (n + kSTile - 1) / kSTile;
-    if (g->ntiles < 1) g->ntiles = 1;
-    PG_CUDA_TRY(ctx, A((void**)&g->scan_total, sizeof(int64_t) * (2 * g->ntiles + 2)));
-    // big-parent scratch shares the plist-sized buffers: bigslot lives in wgt? no - own arrays
-    PG_CUDA_TRY(ctx, A((void**)&g->tile_e, sizeof(int32_t) * n));  // bigslot
-    PG_CUDA_TRY(ctx, A((void**)&g->tile_o, sizeof(int32_t) * n));  // bigfill
-    cudaStream_t s = ctx->stream;
-    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
-    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->head, 0xff, sizeof(int32_t) * n, s));
-    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->tile_e, 0xff, sizeof(int32_t) * n, s));
-    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->tile_o, 0, sizeof(int32_t) * n, s));
+    PG_CUDA_TRY(ctx, cudaMallocHost((void**)&g->hcnt, sizeof(Counters)));
+    g->scan_tmp_bytes = scan_tmp_bytes(n + 2) + 64;
+    PG_CUDA_TRY(ctx, A(&g->scan_tmp, g->scan_tmp_bytes));
+    // co-resident blocks for the cooperative kernels
+    int sms = 0, a = 0, b = 0;
+    PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump_coop, kBlock, 0));
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_idscan_coop, kBlock, 0));
+    g->coop_blocks = sms * std::max(1, std::min(std::min(a, b), 4));
     for (int i = 0; i < 4; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->ev[i]));
     for (int i = 0; i < 2 * KID_COUNT; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->kev[i]));
+    return reset_scratch(g);
+}
+
+pg_status reset_scratch(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    int64_t n = g->n;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->oddsz, 0, sizeof(int32_t) * n, s));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->ccnt, 0, sizeof(int32_t) * (n + 1), s));
     return PG_OK;
 }
 
-pg_status valuate_device(pg_game* g, bool want_dom, Counters* h) {
+pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     int32_t n = g->n;
     Counters* c = g->cnt;
-    unsigned grid = grid_for(n);
+    const unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_gwalk<<<grid, kBlock, 0, s>>>(n, g->strat, g->gd, g->plist, c);
+    k_walk<<<grid, kBlock, 0, s>>>(n, g->strat, g->gd, g->gd32, g->plist, c);
     prof_end(g, KID_WALK, 1);
-    PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_pending, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    prof_collect(g);
-    int32_t np = ctx->pinned[0];
-    if (np > 0) {
-        int rounds = 0;
-        int cap = 96;
+    {
+        int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
-        for (;;) {
-            PG_CUDA_TRY(ctx, cudaMemsetAsync(&c->n_pending, 0, sizeof(int32_t), s));
-            prof_begin(g, KID_JUMP);
-            k_jump<<<grid_for(np), kBlock, 0, s>>>(np, g->plist, g->gd, c);
-            prof_end(g, KID_JUMP, 1);
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_pending, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            prof_collect(g);
-            if (ctx->pinned[0] == 0) break;
-            if (++rounds > cap) return fail(ctx, PG_ECUDA, "valuation: pointer jumping did not converge");
-        }
+        void* args[] = {(void*)&g->plist, (void*)&g->gd, (void*)&g->gd32, (void*)&c, (void*)&cap};
+        prof_begin(g, KID_JUMP);
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
+        prof_end(g, KID_JUMP, 1);
     }
     prof_begin(g, KID_CHAIN1);
-    k_chain1<<<grid, kBlock, 0, s>>>(n, g->gd, g->flags, g->pri, g->cls, g->kind, g->depth, g->sz, g->head, g->nxt,
-                                     g->dom, want_dom ? 1 : 0, c);
+    k_chain1<<<grid, kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls, g->dom,
+                                     want_dom ? 1 : 0, c);
     prof_end(g, KID_CHAIN1, 1);
-    prof_begin(g, KID_PARENTS);
-    k_parents<<<grid, kBlock, 0, s>>>(n, g->head, g->nxt, g->sz, g->flags, g->wgt, g->oddsz, g->biglist, c);
-    prof_end(g, KID_PARENTS, 1);
-    int32_t* bigslot = g->tile_e;
-    int32_t* bigfill = g->tile_o;
-    int32_t* hugelist = g->plist;  // pending list is no longer needed
-    // big parents: their children are collected into kBlockChildren-entry slots of a buffer that borrows
-    // key (rewritten by k_chain2 afterwards); parents are processed in batches that fit.
-    int32_t* bigbuf = g->key;
-    PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &c->n_big, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    prof_collect(g);
-    int32_t nbig = ctx->pinned[0];
-    if (nbig > 0) {
-        int64_t cap_parents = (int64_t)n / kBlockChildren;
-        if (cap_parents < 1) cap_parents = 1;
-        // process big parents in batches that fit in the buffer
-        std::vector<int32_t> hb((size_t)nbig);
-        PG_CUDA_TRY(ctx, cudaMemcpyAsync(hb.data(), g->biglist, sizeof(int32_t) * nbig, cudaMemcpyDeviceToHost, s));
-        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        std::vector<int32_t> huge;
-        for (int64_t b0 = 0; b0 < nbig; b0 += cap_parents) {
-            int32_t cnt_b = (int32_t)std::min<int64_t>(cap_parents, nbig - b0);
-            Counters hc;
-            // stage this batch into biglist[0..cnt_b)
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(g->biglist, hb.data() + b0, sizeof(int32_t) * cnt_b,
-                                             cudaMemcpyHostToDevice, s));
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(&c->n_big, &cnt_b, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-            PG_CUDA_TRY(ctx, cudaMemsetAsync(&c->pad, 0, sizeof(int32_t), s));
-            prof_begin(g, KID_BIG);
-            k_big_mark<<<grid_for(cnt_b), kBlock, 0, s>>>(g->biglist, bigslot, c);
-            k_big_collect<<<grid, kBlock, 0, s>>>(n, g->gd, g->kind, bigslot, bigfill, bigbuf, c);
-            k_big_parents<<<(unsigned)std::min<int64_t>(cnt_b, 152 * 4), kBlock, 0, s>>>(
-                g->biglist, bigslot, bigfill, bigbuf, g->sz, g->flags, g->wgt, g->oddsz, hugelist, c);
-            prof_end(g, KID_BIG, 3);
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(&hc, c, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-            PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            prof_collect(g);
-            if (hc.pad > 0) {
-                size_t old = huge.size();
-                huge.resize(old + hc.pad);
-                PG_CUDA_TRY(ctx, cudaMemcpyAsync(huge.data() + old, hugelist, sizeof(int32_t) * hc.pad,
-                                                 cudaMemcpyDeviceToHost, s));
-                PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            }
-        }
-        // huge parents: one id-ordered scan each
-        for (int32_t p : huge) {
-            ctx->launches += 3;
-            k_idscan_reduce<false><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, p, g->kind, g->gd, g->sz, g->flags,
-                                                                          g->scan_total);
-            k_idscan_tiles<<<1, kBlock, 0, s>>>(g->scan_total, g->ntiles);
-            k_idscan_apply<false><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, p, g->kind, g->gd, g->sz, g->flags,
-                                                                         g->scan_total, g->ntiles, g->wgt,
-                                                                         g->oddsz + p);
-        }
-    }
-    // the sink's children
+    prof_begin(g, KID_CSCAN);
+    PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
+    prof_end(g, KID_CSCAN, 3);
+    prof_begin(g, KID_SCATTER);
+    k_scatter<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval);
+    prof_end(g, KID_SCATTER, 1);
+    prof_begin(g, KID_SIBLINGS);
+    k_siblings<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->slot, g->coff, g->cl_ks, g->wgt, g->oddsz, g->hugelist,
+                                       c);
+    prof_end(g, KID_SIBLINGS, 1);
     prof_begin(g, KID_SINKSCAN);
-    k_idscan_reduce<true><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, n, g->kind, g->gd, g->sz, g->flags,
-                                                                 g->scan_total);
-    k_idscan_tiles<<<1, kBlock, 0, s>>>(g->scan_total, g->ntiles);
-    k_idscan_apply<true><<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, n, g->kind, g->gd, g->sz, g->flags,
-                                                                g->scan_total, g->ntiles, g->wgt, &c->sink_rank);
-    prof_end(g, KID_SINKSCAN, 3);
+    {
+        int64_t ntiles = g->ntiles;
+        void* args[] = {(void*)&n,        (void*)&g->gd32,   (void*)&g->sz,  (void*)&g->kind,  (void*)&g->hugelist,
+                        (void*)&g->tiles, (void*)&ntiles,    (void*)&g->wgt, (void*)&g->oddsz, (void*)&c};
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_idscan_coop, g->coop_blocks, kBlock, args, 0, s));
+        k_sink_reduce<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles);
+        k_tiles_scan<<<1, kBlock, 0, s>>>(g->tiles, g->ntiles);
+        k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->ntiles, g->wgt, c);
+    }
+    prof_end(g, KID_SINKSCAN, 4);
     prof_begin(g, KID_CHAIN2);
-    k_chain2<<<grid, kBlock, 0, s>>>(n, g->gd, g->kind, g->wgt, g->oddsz, g->key, g->sz, g->head, c);
+    k_chain2<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key, g->sz, c);
     prof_end(g, KID_CHAIN2, 1);
-    PG_CUDA_TRY(ctx, cudaMemcpyAsync(h, c, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    prof_collect(g);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
 
-pg_status switch_device(pg_game* g, int player, int32_t* nswitch) {
+pg_status enqueue_depth(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    ctx->launches += 1;
+    k_depth<<<grid_for(g->n), kBlock, 0, ctx->stream>>>(g->n, g->gd, g->kind, g->depth);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_switch(pg_game* g, int player) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
@@ -754,11 +763,18 @@ pg_status switch_device(pg_game* g, int player, int32_t* nswitch) {
     prof_begin(g, kid);
     k_switch<<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->key, g->strat, g->cnt);
     prof_end(g, kid, 1);
-    PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, &g->cnt->n_switch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status sync_counters(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(g->hcnt, g->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     prof_collect(g);
-    PG_CUDA_TRY(ctx, cudaGetLastError());
-    *nswitch = ctx->pinned[0];
+    if (g->hcnt->err & kErrBarrier) return fail(ctx, PG_ECUDA, "valuation: a grid barrier timed out");
+    if (g->hcnt->err & kErrJumpRounds) return fail(ctx, PG_ECUDA, "valuation: pointer jumping did not converge");
     return PG_OK;
 }
 
