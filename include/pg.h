@@ -172,6 +172,39 @@ pg_status pg_reset_stats(pg_game *game);
 /* Number of kernels launched through ctx since it was created. */
 pg_status pg_launch_count(const pg_ctx *ctx, int64_t *out);
 
+/* Valuation of one successor function without allocating any memory. The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory themselves or let a library do it, for example code
+ * running while a CUDA graph is being captured, or a host framework that owns
+ * every device allocation. Instead of per-game buffers it uses one fixed array
+ * compiled into the library (about 18 MB of device memory, held by every GPU
+ * that loads the library until the process exits).
+ *
+ * Input, all device pointers owned by the caller:
+ *   n     vertex count, 1 <= n <= 262,144 (2^18); larger n returns PG_EUNSUPPORTED
+ *         without touching the device;
+ *   succ  n entries: the successor of each vertex under a profile, or n for the sink;
+ *   odd   n entries: 1 if the vertex's priority is odd, 0 if even.
+ * Vertex ids must already be priority ranks (vertex v has the v-th smallest of n
+ * distinct priorities); pg_valuate relabels games this way internally.
+ * Output, device pointers owned by the caller (each may be NULL): val_class,
+ * val_depth and val_rank with the meaning given at the top of this file; ranks
+ * are positions among the finite valuations of these n vertices and the sink.
+ * stream: a cudaStream_t (NULL = the legacy default stream); the call returns
+ * after its work on the stream is complete.
+ *
+ * Returns PG_OK, PG_ENOTADMISSIBLE if a play reaches a cycle whose largest
+ * priority is odd (outputs are still filled), PG_EINVAL for a NULL input or a
+ * successor outside [0, n], PG_ECUDA for a CUDA error. No message is recorded.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * fixed array's device address and the cooperative launch size; make that
+ * first call before any stream capture. All calls share the array and it keeps
+ * the last call's contents (each call clears what must start at zero), so calls
+ * that overlap on the GPU, from any thread or stream, race: serialise them. */
+pg_status pg_valuate_static(int32_t n, const int32_t *succ, const uint8_t *odd, int8_t *val_class,
+                            int32_t *val_depth, int32_t *val_rank, void *stream);
+
 /* Per-phase device time of the last pg_solve / pg_best_response / pg_valuate
  * on game, in milliseconds, measured with CUDA events on the context's stream
  * when timing is enabled (pg_set_timing). Each pointer may be NULL. */

@@ -10,15 +10,16 @@
 
 namespace pg {
 
-pg_status fail(pg_ctx* ctx, pg_status code, const std::string& msg) {
-    if (ctx) ctx->err = msg;
+pg_status fail(pg_ctx* ctx, pg_status code, const char* msg) {
+    if (ctx && !ctx->quiet) ctx->err = msg;
     return code;
 }
 
 pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where) {
-    std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
-    if (ctx) ctx->err = m;
-    return e == cudaErrorMemoryAllocation ? PG_ENOMEM : PG_ECUDA;
+    pg_status code = e == cudaErrorMemoryAllocation ? PG_ENOMEM : PG_ECUDA;
+    if (!ctx || ctx->quiet) return code;
+    ctx->err = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
+    return code;
 }
 
 void free_game(pg_game* g) {

@@ -108,6 +108,7 @@ struct pg_ctx {
     bool timing = false;
     int32_t* pinned = nullptr;  // small pinned host buffer for counters
     int64_t launches = 0;       // kernels launched through this context
+    bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
 };
 
 struct pg_game {
@@ -168,12 +169,14 @@ struct pg_game {
 
 // internal entry points shared by the translation units
 namespace pg {
-pg_status fail(pg_ctx* ctx, pg_status code, const std::string& msg);
+pg_status fail(pg_ctx* ctx, pg_status code, const char* msg);
 pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where);
 pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const int32_t* tgt,
                     const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out);
 pg_status alloc_scratch(pg_game* g);
 void free_game(pg_game* g);
+// Co-resident blocks of the cooperative valuation kernels on a device.
+pg_status coop_blocks_for(pg_ctx* ctx, int* out);
 // per-kernel timing: events around a kernel class on the game's stream
 void prof_begin(pg_game* g, int id);
 void prof_end(pg_game* g, int id, int nlaunch);

@@ -687,6 +687,15 @@ pg_status alloc_scratch(pg_game* g) {
     return reset_scratch(g);
 }
 
+pg_status coop_blocks_for(pg_ctx* ctx, int* out) {
+    int sms = 0, a = 0, b = 0;
+    PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump_coop, kBlock, 0));
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_idscan_coop, kBlock, 0));
+    *out = sms * std::max(1, std::min(std::min(a, b), 4));
+    return PG_OK;
+}
+
 pg_status reset_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;

@@ -86,10 +86,11 @@ def lib():
     L.pg_set_timing.argtypes = [P, I32]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(I64)]
+    L.pg_valuate_static.argtypes = [I32, P, P, P, P, P, P]
     L.pg_kernel_stats.argtypes = [P, C.POINTER(pg_kernel_stat), I32, C.POINTER(I32)]
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
-    for name in ["pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
+    for name in ["pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -242,6 +243,26 @@ def pg_valuate(ctx, game, sigma=None, tau=None, dummy_sigma=None, val_class=None
                           _same_kind(sigma, tau, dummy_sigma), C.byref(val))
     if rc not in (PG_OK, PG_ENOTADMISSIBLE):
         _check(ctx, rc, "pg_valuate")
+    return rc
+
+
+def pg_valuate_static(n, succ, odd, val_class=None, val_depth=None, val_rank=None, stream=None):
+    """Allocation-free valuation of a successor function whose vertex ids are
+    priority ranks (device arrays only). Returns the status code (PG_OK or
+    PG_ENOTADMISSIBLE; any other status raises PgError)."""
+    arrays = [succ, odd, val_class, val_depth, val_rank]
+    if any(a is not None and _ptr_kind(a)[1] != PG_MEM_DEVICE for a in arrays):
+        raise ValueError("pg_valuate_static takes device arrays only")
+    _dtype_check(succ, np.int32, "succ")
+    _dtype_check(odd, np.uint8, "odd")
+    _dtype_check(val_class, np.int8, "val_class")
+    _dtype_check(val_depth, np.int32, "val_depth")
+    _dtype_check(val_rank, np.int32, "val_rank")
+    handle = getattr(stream, "cuda_stream", stream)
+    rc = lib().pg_valuate_static(int(n), _ptr_kind(succ)[0], _ptr_kind(odd)[0], _ptr_kind(val_class)[0],
+                                 _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], C.c_void_p(handle or None))
+    if rc not in (PG_OK, PG_ENOTADMISSIBLE):
+        raise PgError(rc, "pg_valuate_static failed")
     return rc
 
 
