@@ -15,14 +15,14 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pg.h"
+#include "pg.h"
 
 namespace pg {
 
 constexpr int kBlock = 256;
 constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
-constexpr int kCoopTile = 2048;       // elements per tile of the cooperative id-ordered scan
+constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
 
 // flags[v]
 constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
@@ -60,6 +60,7 @@ struct Counters {
     int32_t n_fin;       // finite vertices
     int32_t n_odd;       // vertices reaching an odd cycle
     int32_t n_huge;      // parents ranked by the id-ordered scan
+    int32_t n_big;       // parents ranked by one block each
     int32_t n_switch;    // switched vertices in the last switching pass
     int32_t err;         // device-side error bits (kErr*)
     int32_t sink_rank;   // rank of the sink's empty valuation

@@ -46,6 +46,12 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+inline unsigned ilp_grid(int64_t n) {
+    int64_t tiles = (n + 32 * 4 - 1) / (32 * 4);
+    int64_t b = (tiles + kBlock / 32 - 1) / (kBlock / 32);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
 inline unsigned grid_for(int64_t n) {
     int64_t b = (n + kBlock - 1) / kBlock;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
@@ -78,12 +84,12 @@ __device__ inline uint64_t ld_cg(const uint64_t* p) { return __ldcg((const unsig
 __device__ inline void st_cg(uint64_t* p, uint64_t v) { __stcg((unsigned long long*)p, (unsigned long long)v); }
 
 // Compact g-word read by every chain pass: bit 31 = "none" (v is above its
-// whole infinite future; the low bits then name the cycle maximum), low 31
-// bits = g(v) (a vertex or the sink id n).
+// whole infinite future; the low bits then name the cycle maximum), low 30
+// bits = g(v) (a vertex or the sink id n; n < 2^30).
 constexpr uint32_t kG32None = 0x80000000u;
 __device__ inline uint32_t g32_of(uint64_t w) { return (gd_none(w) ? kG32None : 0u) | (uint32_t)gd_ptr(w); }
 __device__ inline bool g32_none(uint32_t w) { return (w & kG32None) != 0; }
-__device__ inline int32_t g32_ptr(uint32_t w) { return (int32_t)(w & 0x7fffffffu); }
+__device__ inline int32_t g32_ptr(uint32_t w) { return (int32_t)(w & 0x3fffffffu); }
 
 // kind[v], written by k_chain1
 constexpr uint8_t kKFin = 1;        // finite valuation
@@ -124,36 +130,71 @@ __device__ bool grid_sync(Counters* c) {
 }
 
 // ---------------------------------------------------------------------------
+// Pointer-chasing passes give each thread kIlp vertices, v + 32 j for
+// j < kIlp within a warp tile of 32 kIlp vertices: per-vertex reads and writes
+// stay coalesced for every j, and the walks of one thread issue their gathers
+// together, so each thread keeps kIlp loads in flight.
+constexpr int kIlp = 4;
+
+__device__ inline int64_t warp_tile_base(int64_t tile) { return tile * 32 * kIlp; }
+
 // K1: nearest greater vertex along the play, by a direct walk of at most
-// kWalkCap steps (one thread per vertex, so the first read and the final
-// write of each warp are coalesced). A walk that returns to its start found
-// the maximum of its cycle; a walk that runs out of steps leaves a jump
-// pointer for k_jump_coop.
+// kWalkCap steps. A walk that returns to its start found the maximum of its
+// cycle; a walk that runs out of steps leaves a jump pointer for k_jump_coop.
 __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __restrict__ strat,
                                                  uint64_t* __restrict__ gd, uint32_t* __restrict__ gd32,
-                                                 int32_t* __restrict__ plist, Counters* cnt) {
-    for (int32_t v0 = blockIdx.x * blockDim.x; v0 < n; v0 += gridDim.x * blockDim.x) {
-        const int32_t v = v0 + threadIdx.x;
-        bool pend = false;
-        if (v < n) {
-            int32_t x = __ldg(strat + v);
-            uint32_t d = 1;
-            while (x < v && d < (uint32_t)kWalkCap) {
-                x = __ldg(strat + x);
-                ++d;
-            }
-            uint64_t w;
-            if (x > v) w = gd_pack(true, false, d, x);       // a larger vertex or the sink
-            else if (x == v) w = gd_pack(true, true, d, v);  // v is the maximum of its cycle
-            else {
-                w = gd_pack(false, false, d, x);
-                pend = true;
-            }
-            gd[v] = w;
-            gd32[v] = g32_of(w);
+                                                 int32_t* __restrict__ plist, int32_t* __restrict__ sz,
+                                                 int32_t* __restrict__ oddsz, Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], x[kIlp];
+        uint32_t d[kIlp];
+        bool act[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            x[j] = v[j] < n ? __ldg(strat + v[j]) : n;
+            d[j] = 1;
         }
-        int32_t slot = warp_append(pend, &cnt->n_pending);
-        if (pend) plist[slot] = v;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
+        for (;;) {
+            bool any = false;
+            int32_t nx[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    x[j] = nx[j];
+                    ++d[j];
+                    act[j] = x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            bool pend = false;
+            if (v[j] < n) {
+                uint64_t w;
+                if (x[j] > v[j]) w = gd_pack(true, false, d[j], x[j]);       // a larger vertex or the sink
+                else if (x[j] == v[j]) w = gd_pack(true, true, d[j], v[j]);  // v is the maximum of its cycle
+                else {
+                    w = gd_pack(false, false, d[j], x[j]);
+                    pend = true;
+                }
+                gd[v[j]] = w;
+                gd32[v[j]] = g32_of(w);
+                sz[v[j]] = 0;  // zeros for this valuation's size and odd-total accumulation
+                oddsz[v[j]] = 0;
+            }
+            int32_t slot = warp_append(pend, &cnt->n_pending);
+            if (pend) plist[slot] = v[j];
+        }
     }
 }
 
@@ -214,50 +255,95 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
 // Classification and g-subtree sizes. Each vertex walks its g-chain (4-byte
 // words) to its end: the sink means a finite valuation, a "none" vertex
 // means TOP (odd cycle if that cycle maximum is odd). Finite vertices then
-// add one to each g-ancestor below the sink (the second walk hits cache) and
-// take a slot among their g-parent's children. TOP vertices touch nothing
-// else, so large TOP components cause no atomic hot spots.
+// take a slot among their g-parent's children and add one to each g-ancestor
+// below the sink. TOP vertices touch nothing else, so large TOP components
+// cause no atomic hot spots.
 __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __restrict__ gd32,
                                                    const uint8_t* __restrict__ flags, const int32_t* __restrict__ pri,
                                                    int32_t* sz, int32_t* ccnt, int32_t* __restrict__ slot,
                                                    uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
                                                    int32_t* __restrict__ dom, int want_dom, Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t nfin = 0, nodd = 0;
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint32_t w = gd32[v];
-        const bool odd_v = (flags[v] & kPriOdd) != 0;
-        int32_t cyc = -1;
-        if (g32_none(w)) {
-            cyc = g32_ptr(w);
-        } else {
-            for (int32_t x = g32_ptr(w); x != n;) {
-                uint32_t wx = gd32[x];
-                if (g32_none(wx)) {
-                    cyc = g32_ptr(wx);
-                    break;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], g[kIlp], x[kIlp], cyc[kIlp];
+        bool act[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            const uint32_t w = v[j] < n ? gd32[v[j]] : (uint32_t)n;
+            g[j] = g32_ptr(w);
+            cyc[j] = g32_none(w) ? g[j] : -1;
+            x[j] = g[j];
+            act[j] = v[j] < n && !g32_none(w) && g[j] != n;
+        }
+        // classification walks
+        for (;;) {
+            bool any = false;
+            uint32_t wx[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    if (g32_none(wx[j])) {
+                        cyc[j] = g32_ptr(wx[j]);
+                        act[j] = false;
+                    } else {
+                        x[j] = g32_ptr(wx[j]);
+                        act[j] = x[j] != n;
+                    }
                 }
-                x = g32_ptr(wx);
+                any |= act[j];
             }
+            if (!any) break;
         }
-        int32_t sl = -1;
-        if (cyc < 0) {
-            const int32_t g = g32_ptr(w);
-            kind[v] = kKFin | (g == n ? kKSinkChild : 0) | (odd_v ? kKOdd : 0);
-            cls[v] = kFin;
-            if (want_dom) dom[v] = -1;
-            if (g != n) {
-                sl = atomicAdd(ccnt + g, 1);
-                for (int32_t x = g; x != n; x = g32_ptr(gd32[x])) atomicAdd(sz + x, 1);
+        // finite vertices below a vertex parent: slot, then sizes along the chain
+        int32_t sl[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            act[j] = v[j] < n && cyc[j] < 0 && g[j] != n;
+            sl[j] = act[j] ? atomicAdd(ccnt + g[j], 1) : -1;
+            x[j] = g[j];
+        }
+        for (;;) {
+            bool any = false;
+            uint32_t wx[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) atomicAdd(sz + x[j], 1);
+                wx[j] = act[j] ? gd32[x[j]] : 0u;
             }
-            ++nfin;
-        } else {
-            const bool odd = (flags[cyc] & kPriOdd) != 0;
-            kind[v] = 0;
-            cls[v] = odd ? kOddCycle : kTop;
-            if (want_dom) dom[v] = pri[cyc];
-            nodd += odd;
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    x[j] = g32_ptr(wx[j]);
+                    act[j] = x[j] != n;
+                }
+                any |= act[j];
+            }
+            if (!any) break;
         }
-        slot[v] = sl;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (v[j] >= n) continue;
+            if (cyc[j] < 0) {
+                const bool odd_v = (flags[v[j]] & kPriOdd) != 0;
+                kind[v[j]] = kKFin | (g[j] == n ? kKSinkChild : 0) | (odd_v ? kKOdd : 0);
+                cls[v[j]] = kFin;
+                if (want_dom) dom[v[j]] = -1;
+                ++nfin;
+            } else {
+                const bool odd = (flags[cyc[j]] & kPriOdd) != 0;
+                kind[v[j]] = 0;
+                cls[v[j]] = odd ? kOddCycle : kTop;
+                if (want_dom) dom[v[j]] = pri[cyc[j]];
+                nodd += odd;
+            }
+            slot[v[j]] = sl[j];
+        }
     }
     block_add(nfin, &cnt->n_fin);
     block_add(nodd, &cnt->n_odd);
@@ -288,35 +374,138 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* _
     if (blockIdx.x == 0 && threadIdx.x == 0) ccnt[n] = 0;
 }
 
-// Sibling weights, one thread per finite vertex with a vertex parent: sum
-// the sizes of the siblings ordered before it in the parent's segment; the
-// child in slot 0 also writes the parent's odd total. Segments above
-// kHugeChildren are left to k_idscan_coop.
-__global__ void __launch_bounds__(kBlock) k_siblings(int32_t n, const uint32_t* __restrict__ gd32,
-                                                     const uint8_t* __restrict__ kind,
-                                                     const int32_t* __restrict__ slot,
-                                                     const int32_t* __restrict__ coff, const int2* __restrict__ cl_ks,
-                                                     int32_t* __restrict__ wgt, int32_t* __restrict__ oddsz,
+// Sibling weights, one thread per parent (coalesced segment offsets): for
+// each child in the parent's segment, the sizes of the siblings ordered
+// before it, plus one for even children; the parent's odd total goes to
+// oddsz. Segments of up to kSmallChildren children are done here;
+// larger ones are queued for k_big_parents (up to kHugeChildren) or for the
+// id-ordered scan (beyond).
+constexpr int kSmallChildren = 32;
+
+__device__ inline int32_t child_of_key(int32_t k) { return k >= 0 ? k : -k - 1; }
+
+__global__ void __launch_bounds__(kBlock) k_siblings(int32_t n, const int32_t* __restrict__ coff,
+                                                     const int2* __restrict__ cl_ks, int32_t* __restrict__ wgt,
+                                                     int32_t* __restrict__ oddsz, int32_t* biglist,
                                                      int32_t* hugelist, Counters* cnt) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint8_t kd = kind[v];
-        if (!(kd & kKFin) || (kd & kKSinkChild)) continue;
-        const int32_t a = g32_ptr(gd32[v]);
-        const int32_t s0 = coff[a], s1 = coff[a + 1];
-        const bool first = slot[v] == 0;
-        if (s1 - s0 > kHugeChildren) {
-            if (first) hugelist[atomicAdd(&cnt->n_huge, 1)] = a;
-            continue;
+    const int lane = threadIdx.x & 31;
+    for (int32_t a0 = blockIdx.x * blockDim.x; a0 < n; a0 += gridDim.x * blockDim.x) {
+        const int32_t a = a0 + threadIdx.x;
+        int32_t s0 = 0, k = 0;
+        if (a < n) {
+            s0 = coff[a];
+            k = coff[a + 1] - s0;
         }
-        const int32_t myk = order_key(v, (kd & kKOdd) != 0);
-        int32_t pre = 0, os = 0;
-        for (int32_t q = s0; q < s1; ++q) {
-            int2 ks = __ldg(cl_ks + q);
-            if (ks.x < myk) pre += ks.y;
-            if (ks.x < 0) os += ks.y;
+        if (k > kHugeChildren) hugelist[atomicAdd(&cnt->n_huge, 1)] = a;
+        else if (k > kSmallChildren) biglist[atomicAdd(&cnt->n_big, 1)] = a;
+        else if (k > 0 && k <= 4) {  // few children: this thread alone
+            int32_t os = 0;
+            for (int32_t i = s0; i < s0 + k; ++i) {
+                const int2 ki = __ldg(cl_ks + i);
+                int32_t pre = 0;
+                for (int32_t j = s0; j < s0 + k; ++j) {
+                    const int2 kj = __ldg(cl_ks + j);
+                    if (kj.x < ki.x) pre += kj.y;
+                }
+                wgt[child_of_key(ki.x)] = pre + (ki.x >= 0 ? 1 : 0);
+                if (ki.x < 0) os += ki.y;
+            }
+            oddsz[a] = os;
         }
-        wgt[v] = pre + (myk >= 0 ? 1 : 0);
-        if (first) oddsz[a] = os;
+        // 5..kSmallChildren children: the whole warp, one lane per child
+        unsigned mid = __ballot_sync(kFull, k > 4 && k <= kSmallChildren);
+        while (mid) {
+            const int src = __ffs(mid) - 1;
+            mid &= mid - 1;
+            const int32_t pa = __shfl_sync(kFull, a, src), ps0 = __shfl_sync(kFull, s0, src),
+                          pk = __shfl_sync(kFull, k, src);
+            const int2 mine = lane < pk ? __ldg(cl_ks + ps0 + lane) : make_int2(INT32_MAX, 0);
+            int32_t pre = 0;
+            for (int j = 0; j < pk; ++j) {
+                const int32_t kx = __shfl_sync(kFull, mine.x, j), ky = __shfl_sync(kFull, mine.y, j);
+                if (kx < mine.x) pre += ky;
+            }
+            int32_t os = (lane < pk && mine.x < 0) ? mine.y : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) os += __shfl_down_sync(kFull, os, o);
+            if (lane < pk) wgt[child_of_key(mine.x)] = pre + (mine.x >= 0 ? 1 : 0);
+            if (lane == 0) oddsz[pa] = os;
+        }
+    }
+}
+
+// One block per big parent (kSmallChildren < k <= kHugeChildren): the
+// segment is sorted by order key in shared memory and scanned.
+__global__ void __launch_bounds__(kBlock) k_big_parents(const int32_t* __restrict__ coff,
+                                                        const int2* __restrict__ cl_ks,
+                                                        const int32_t* __restrict__ biglist,
+                                                        int32_t* __restrict__ wgt, int32_t* __restrict__ oddsz,
+                                                        const Counters* cnt) {
+    __shared__ int2 sk[kHugeChildren];
+    __shared__ int32_t wsum[kBlock / 32];
+    __shared__ int32_t carry_s, odd_s;
+    const int32_t nb = cnt->n_big;
+    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int32_t a = biglist[b];
+        const int32_t s0 = coff[a], count = coff[a + 1] - s0;
+        int p2 = 1;
+        while (p2 < count) p2 <<= 1;
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = i < count ? cl_ks[s0 + i] : make_int2(INT32_MAX, 0);
+        __syncthreads();
+        for (int kk = 2; kk <= p2; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int2 x = sk[i], y = sk[ixj];
+                        const bool up = (i & kk) == 0;
+                        if ((x.x > y.x) == up) {
+                            sk[i] = y;
+                            sk[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            carry_s = 0;
+            odd_s = 0;
+        }
+        __syncthreads();
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int base = 0; base < count; base += blockDim.x) {
+            const int i = base + threadIdx.x;
+            const int2 e = i < count ? sk[i] : make_int2(0, 0);
+            const int32_t sv = i < count ? e.y : 0;
+            int32_t x = sv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[wid] = x;
+            __syncthreads();
+            if (wid == 0) {
+                int32_t t = lane < kBlock / 32 ? wsum[lane] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(kFull, t, o);
+                    if (lane >= o) t += y;
+                }
+                if (lane < kBlock / 32) wsum[lane] = t;
+            }
+            __syncthreads();
+            if (i < count) {
+                wgt[child_of_key(e.x)] = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - sv + (e.x >= 0 ? 1 : 0);
+                if (e.x < 0) atomicAdd(&odd_s, sv);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) carry_s += wsum[kBlock / 32 - 1];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) oddsz[a] = odd_s;
+        __syncthreads();
     }
 }
 
@@ -374,12 +563,17 @@ __device__ inline void block_scan2(int32_t ve, int32_t vo, int64_t* xe, int64_t*
     __syncthreads();
 }
 
-// eight consecutive sinkval entries of thread t in tile b (two 16-byte loads)
+// kCIpt consecutive sinkval entries starting at i0 (16-byte loads when full)
 __device__ inline void load8(const int32_t* __restrict__ sinkval, int32_t n, int64_t i0, int32_t v[kCIpt]) {
     if (i0 + kCIpt <= n) {
-        int4 a = __ldg(reinterpret_cast<const int4*>(sinkval + i0));
-        int4 b = __ldg(reinterpret_cast<const int4*>(sinkval + i0) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+        for (int q = 0; q < kCIpt / 4; ++q) {
+            int4 a = __ldg(reinterpret_cast<const int4*>(sinkval + i0) + q);
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < kCIpt; ++k) v[k] = i0 + k < n ? sinkval[i0 + k] : 0;
@@ -407,19 +601,50 @@ __global__ void __launch_bounds__(kBlock) k_sink_reduce(int32_t n, const int32_t
 }
 
 // exclusive scan of the (even, odd) tile sums by one block; totals after the last tile
-__global__ void __launch_bounds__(kBlock) k_tiles_scan(int64_t* tiles, int64_t ntiles) {
+constexpr int kTileScanThreads = 1024;
+
+__global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* tiles, int64_t ntiles) {
+    __shared__ int64_t se[kTileScanThreads / 32], so[kTileScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t ce = 0, co = 0;
-    for (int64_t b = 0; b < ntiles; b += kBlock) {
-        int64_t i = b + threadIdx.x;
-        int64_t e = i < ntiles ? tiles[2 * i] : 0, o = i < ntiles ? tiles[2 * i + 1] : 0;
-        int64_t xe, xo, te, to;
-        block_scan2((int32_t)e, (int32_t)o, &xe, &xo, &te, &to);
-        if (i < ntiles) {
-            tiles[2 * i] = ce + xe;
-            tiles[2 * i + 1] = co + xo;
+    for (int64_t b = 0; b < ntiles; b += kTileScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t e = i < ntiles ? tiles[2 * i] : 0, o = i < ntiles ? tiles[2 * i + 1] : 0;
+        int64_t xa = e, xb = o;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t ya = __shfl_up_sync(kFull, xa, d), yb = __shfl_up_sync(kFull, xb, d);
+            if (lane >= d) {
+                xa += ya;
+                xb += yb;
+            }
         }
-        ce += te;
-        co += to;
+        if (lane == 31) {
+            se[wid] = xa;
+            so[wid] = xb;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            int64_t pa = se[lane], pb = so[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t ya = __shfl_up_sync(kFull, pa, d), yb = __shfl_up_sync(kFull, pb, d);
+                if (lane >= d) {
+                    pa += ya;
+                    pb += yb;
+                }
+            }
+            se[lane] = pa;
+            so[lane] = pb;
+        }
+        __syncthreads();
+        if (i < ntiles) {
+            tiles[2 * i] = ce + (wid > 0 ? se[wid - 1] : 0) + xa - e;
+            tiles[2 * i + 1] = co + (wid > 0 ? so[wid - 1] : 0) + xb - o;
+        }
+        ce += se[kTileScanThreads / 32 - 1];
+        co += so[kTileScanThreads / 32 - 1];
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         tiles[2 * ntiles] = ce;
@@ -539,22 +764,54 @@ __global__ void __launch_bounds__(kBlock) k_idscan_coop(int32_t n, const uint32_
 }
 
 // Ranks: sum the weights along each finite vertex's g-chain (TOP vertices
-// rank above everything). Also restores the between-valuation zeros of sz
-// and oddsz.
+// rank above everything).
 __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __restrict__ gd32,
                                                    const uint8_t* __restrict__ kind, const int32_t* __restrict__ wgt,
-                                                   int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
-                                                   int32_t* __restrict__ sz, const Counters* cnt) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int32_t r = INT32_MAX;
-        if (kind[v] & kKFin) {
-            int32_t acc = oddsz[v] + wgt[v];
-            for (int32_t x = g32_ptr(gd32[v]); x != n; x = g32_ptr(gd32[x])) acc += wgt[x];
-            r = acc;
+                                                   const int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
+                                                   const Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], x[kIlp], acc[kIlp];
+        bool fin[kIlp], act[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            fin[j] = v[j] < n && (kind[v[j]] & kKFin);
+            acc[j] = 0;
+            x[j] = n;
+            if (fin[j]) {
+                acc[j] = oddsz[v[j]] + wgt[v[j]];
+                x[j] = g32_ptr(gd32[v[j]]);
+            }
+            act[j] = fin[j] && x[j] != n;
         }
-        key[v] = r;
-        oddsz[v] = 0;
-        sz[v] = 0;
+        for (;;) {
+            bool any = false;
+            uint32_t wx[kIlp];
+            int32_t wg[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                wx[j] = act[j] ? gd32[x[j]] : 0u;
+                wg[j] = act[j] ? wgt[x[j]] : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    acc[j] += wg[j];
+                    x[j] = g32_ptr(wx[j]);
+                    act[j] = x[j] != n;
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (v[j] >= n) continue;
+            key[v[j]] = fin[j] ? acc[j] : INT32_MAX;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) key[n] = cnt->sink_rank;
 }
@@ -714,7 +971,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     const unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk<<<grid, kBlock, 0, s>>>(n, g->strat, g->gd, g->gd32, g->plist, c);
+    k_walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->gd, g->gd32, g->plist, g->sz, g->oddsz, c);
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;
@@ -725,7 +982,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         prof_end(g, KID_JUMP, 1);
     }
     prof_begin(g, KID_CHAIN1);
-    k_chain1<<<grid, kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls, g->dom,
+    k_chain1<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls, g->dom,
                                      want_dom ? 1 : 0, c);
     prof_end(g, KID_CHAIN1, 1);
     prof_begin(g, KID_CSCAN);
@@ -735,9 +992,9 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     k_scatter<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval);
     prof_end(g, KID_SCATTER, 1);
     prof_begin(g, KID_SIBLINGS);
-    k_siblings<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->slot, g->coff, g->cl_ks, g->wgt, g->oddsz, g->hugelist,
-                                       c);
-    prof_end(g, KID_SIBLINGS, 1);
+    k_siblings<<<grid, kBlock, 0, s>>>(n, g->coff, g->cl_ks, g->wgt, g->oddsz, g->plist, g->hugelist, c);
+    k_big_parents<<<g->coop_blocks, kBlock, 0, s>>>(g->coff, g->cl_ks, g->plist, g->wgt, g->oddsz, c);
+    prof_end(g, KID_SIBLINGS, 2);
     prof_begin(g, KID_SINKSCAN);
     {
         int64_t ntiles = g->ntiles;
@@ -745,12 +1002,12 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
                         (void*)&g->tiles, (void*)&ntiles,    (void*)&g->wgt, (void*)&g->oddsz, (void*)&c};
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_idscan_coop, g->coop_blocks, kBlock, args, 0, s));
         k_sink_reduce<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles);
-        k_tiles_scan<<<1, kBlock, 0, s>>>(g->tiles, g->ntiles);
+        k_tiles_scan<<<1, kTileScanThreads, 0, s>>>(g->tiles, g->ntiles);
         k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->ntiles, g->wgt, c);
     }
     prof_end(g, KID_SINKSCAN, 4);
     prof_begin(g, KID_CHAIN2);
-    k_chain2<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key, g->sz, c);
+    k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key, c);
     prof_end(g, KID_CHAIN2, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpg.so")
+# PG_LIBPG may name another build of the same library (for example a debug build)
+LIB_PATH = os.environ.get("PG_LIBPG") or os.path.join(HERE, "libpg.so")
 
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETIMEOUT, PG_ENOTADMISSIBLE, PG_ECUDA, PG_EUNSUPPORTED = range(7)
 PG_MEM_HOST, PG_MEM_DEVICE = 0, 1
