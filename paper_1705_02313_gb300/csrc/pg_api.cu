@@ -24,7 +24,8 @@ pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where) {
 
 void free_game(pg_game* g) {
     if (!g) return;
-    void* ptrs[] = {g->off,  g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
+    void* ptrs[] = {g->off,  g->off64,   g->vgame, g->gsink, g->gst,   g->gactive, g->gscan,
+                    g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
                     g->tiles, g->cnt,    g->scan_tmp, g->stage};
@@ -47,19 +48,26 @@ inline unsigned grid_of(int64_t n) {
 
 // Sets g->strat from a profile given in original ids (NULL arrays take the
 // defaults: Even and dummies to the sink, Odd to its first edge).
-__global__ void k_apply_profile(int32_t n0, int32_t n, int32_t k, const int32_t* __restrict__ nid0,
-                                const int32_t* __restrict__ off, const int32_t* __restrict__ tgt,
+__device__ inline int32_t sink_id(int32_t i, const int32_t* vgame, const int32_t* gsink, int32_t sink0) {
+    return vgame ? gsink[vgame[i]] : sink0;
+}
+
+template <typename OffT>
+__global__ void k_apply_profile(int64_t n0, int32_t k, const int32_t* __restrict__ nid0,
+                                const OffT* __restrict__ off, const int32_t* __restrict__ tgt,
                                 const uint8_t* __restrict__ flags, const int32_t* __restrict__ orig_of,
-                                const int32_t* __restrict__ dnid, const int32_t* sigma, const int32_t* tau,
-                                const int8_t* dsig, int32_t* strat, int32_t* err) {
+                                const int32_t* __restrict__ dnid, const int32_t* __restrict__ vgame,
+                                const int32_t* __restrict__ gsink, int32_t sink0, const int32_t* sigma,
+                                const int32_t* tau, const int8_t* dsig, int32_t* strat, int32_t* err) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0 + (int64_t)k;
          v += (int64_t)gridDim.x * blockDim.x) {
         if (v >= n0) {
             int32_t d = dnid[v - n0];
-            strat[d] = (dsig && dsig[v - n0]) ? tgt[off[d]] : n;
+            strat[d] = (dsig && dsig[v - n0]) ? tgt[off[d]] : sink_id(d, vgame, gsink, sink0);
             continue;
         }
         int32_t i = nid0[v];
+        const int32_t n = sink_id(i, vgame, gsink, sink0);
         bool odd = (flags[i] & kOwnerOdd) != 0;
         const int32_t* src = odd ? tau : sigma;
         if (!src) {
@@ -72,7 +80,7 @@ __global__ void k_apply_profile(int32_t n0, int32_t n, int32_t k, const int32_t*
             continue;
         }
         int32_t pick = -1;
-        for (int32_t e = off[i]; e < off[i + 1]; ++e)
+        for (OffT e = off[i]; e < off[i + 1]; ++e)
             if (orig_of[tgt[e]] == t) {
                 pick = tgt[e];
                 break;
@@ -97,18 +105,22 @@ struct OutPtrs {
     int8_t* dsig;
 };
 
-__global__ void k_results(int32_t n0, int32_t n, int32_t k, const int32_t* __restrict__ nid0,
+__global__ void k_results(int64_t n0, int32_t k, const int32_t* __restrict__ nid0,
                           const int32_t* __restrict__ dnid, const uint8_t* __restrict__ flags,
                           const int32_t* __restrict__ strat, const uint8_t* __restrict__ cls,
                           const int32_t* __restrict__ depth, const int32_t* __restrict__ key,
-                          const int32_t* __restrict__ orig_of, const int32_t* __restrict__ dom, OutPtrs o) {
+                          const int32_t* __restrict__ orig_of, const int32_t* __restrict__ dom,
+                          const int32_t* __restrict__ vgame, const int32_t* __restrict__ gsink, int32_t sink0,
+                          OutPtrs o) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0 + (int64_t)k;
          v += (int64_t)gridDim.x * blockDim.x) {
         if (v >= n0) {
-            if (o.dsig) o.dsig[v - n0] = strat[dnid[v - n0]] != n;
+            const int32_t d = dnid[v - n0];
+            if (o.dsig) o.dsig[v - n0] = strat[d] != sink_id(d, vgame, gsink, sink0);
             continue;
         }
         int32_t i = nid0[v];
+        const int32_t n = sink_id(i, vgame, gsink, sink0);
         bool fin = cls[i] == kFin;
         bool odd = (flags[i] & kOwnerOdd) != 0;
         int32_t s = strat[i];
@@ -161,9 +173,9 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
         if (st) return st;
     }
     ctx->launches += 1;
-    k_results<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->dnid, g->flags,
-                                                                g->strat, g->cls, g->depth, g->key, g->orig_of,
-                                                                g->dom, o);
+    k_results<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->k, g->nid0, g->dnid, g->flags, g->strat,
+                                                                g->cls, g->depth, g->key, g->orig_of, g->dom,
+                                                                g->vgame, g->gsink, g->sink0, o);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     if (mem_kind == PG_MEM_HOST) {
         size_t n0 = (size_t)g->n0;
@@ -212,9 +224,14 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) {
         ctx->launches += 1;
-        k_apply_profile<<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(g->n0, g->n, g->k, g->nid0, g->off, g->tgt,
-                                                                          g->flags, g->orig_of, g->dnid, ds, dt, dd,
-                                                                          g->strat, err);
+        if (g->off64)
+            k_apply_profile<int64_t><<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(
+                g->n0, g->k, g->nid0, g->off64, g->tgt, g->flags, g->orig_of, g->dnid, g->vgame, g->gsink, g->sink0, ds,
+                dt, dd, g->strat, err);
+        else
+            k_apply_profile<int32_t><<<grid_of((int64_t)g->n0 + g->k), kBlock, 0, s>>>(
+                g->n0, g->k, g->nid0, g->off, g->tgt, g->flags, g->orig_of, g->dnid, g->vgame, g->gsink, g->sink0, ds,
+                dt, dd, g->strat, err);
         e = cudaMemcpyAsync(ctx->pinned, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -243,31 +260,31 @@ struct Timer {
     }
 };
 
-// The inner loop of Algorithm 1: valuations and Odd switches until no Odd
-// vertex switches. The last valuation is left in g (key, cls, depth). One
-// host synchronisation per iteration (the switch count).
-pg_status inner_loop(pg_game* g, int64_t cap, int64_t* inner, Timer& tm, bool* timed_out) {
-    *timed_out = false;
+// Algorithm 1 for every game of g at once: each iteration computes the
+// valuation of every game, switches Odd in active games, switches Even in
+// games whose inner loop has converged (no Odd switch this iteration), and
+// updates each game's state on the device (see k_bookkeep). With even = false
+// only the inner loop runs (best responses). One host synchronisation per
+// iteration: the number of games still active.
+pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
+    pg_ctx* ctx = g->ctx;
     for (;;) {
-        if (*inner >= cap) {
-            *timed_out = true;
-            return PG_OK;
-        }
         tm.mark(0);
         pg_status st = enqueue_valuation(g, false);
         if (st) return st;
         tm.mark(1);
         st = enqueue_switch(g, 1);
+        if (!st && even) st = enqueue_switch(g, 0);
+        if (!st) st = enqueue_bookkeeping(g, cap, even);
         if (st) return st;
         tm.mark(2);
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, g->gactive, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
         st = sync_counters(g);
         if (st) return st;
-        ++*inner;
+        ++g->t_vals;
         g->t_val += tm.since(0, 1);
         g->t_switch += tm.since(1, 2);
-        if (g->hcnt->n_odd > 0)
-            return fail(g->ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
-        if (g->hcnt->n_switch == 0) return PG_OK;
+        if (ctx->pinned[0] == 0) return PG_OK;
     }
 }
 
@@ -387,24 +404,17 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     int64_t cap = (opts && opts->max_inner > 0) ? opts->max_inner : 64 * ((int64_t)g->n + 64);
     pg_status st = apply_profile(g, opts ? opts->sigma_init : nullptr, opts ? opts->tau_init : nullptr,
                                  opts ? opts->dummy_sigma_init : nullptr, opts ? opts->mem_kind : PG_MEM_HOST);
-    if (st) return st;
-    st = reset_scratch(g);
+    if (!st) st = reset_scratch(g);
     if (st) return st;
     Timer tm(g);
     tm.mark(3);
-    int64_t major = 0, inner = 0;
-    bool timed_out = false;
-    for (;;) {
-        st = inner_loop(g, cap, &inner, tm, &timed_out);
-        if (st) return st;
-        if (timed_out) break;
-        st = enqueue_switch(g, 0);
-        if (st) return st;
-        st = sync_counters(g);
-        if (st) return st;
-        if (g->hcnt->n_switch == 0) break;
-        ++major;
-    }
+    st = run_loop(g, cap, true, tm);
+    if (st) return st;
+    GameState gs;
+    PG_CUDA_TRY(ctx, cudaMemcpy(&gs, g->gst, sizeof(gs), cudaMemcpyDeviceToHost));
+    if (gs.phase == kPhaseOddCycle)
+        return fail(ctx, PG_ENOTADMISSIBLE, "pg_solve: an odd cycle was reached: sigma is not admissible");
+    const bool timed_out = gs.phase == kPhaseTimeout;
     if (timed_out) {
         st = enqueue_valuation(g, false);  // valuation of the profile being returned
         if (!st) st = sync_counters(g);
@@ -412,9 +422,8 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     }
     tm.mark(2);
     g->t_total = tm.since(3, 2);
-    g->t_vals = inner;
-    out->major = major;
-    out->inner = inner;
+    out->major = gs.major;
+    out->inner = gs.inner;
     st = write_outputs(g, out->mem_kind, out->win, out->sigma, out->tau, out->val_class, out->val_depth,
                        out->val_rank, nullptr, out->dummy_sigma);
     if (st) return st;
@@ -433,14 +442,16 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
     if (st) return st;
     Timer tm(g);
     tm.mark(3);
-    int64_t inner = 0;
-    bool timed_out = false;
-    st = inner_loop(g, 64 * ((int64_t)g->n + 64), &inner, tm, &timed_out);
-    if (iters_out) *iters_out = inner;
+    st = run_loop(g, 64 * ((int64_t)g->n + 64), false, tm);
     if (st) return st;
+    GameState gs;
+    PG_CUDA_TRY(ctx, cudaMemcpy(&gs, g->gst, sizeof(gs), cudaMemcpyDeviceToHost));
+    if (iters_out) *iters_out = gs.inner;
+    if (gs.phase == kPhaseOddCycle)
+        return fail(ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
+    const bool timed_out = gs.phase == kPhaseTimeout;
     tm.mark(2);
     g->t_total = tm.since(3, 2);
-    g->t_vals = inner;
     st = write_outputs(g, mem_kind, nullptr, nullptr, tau_inout, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (st) return st;
     if (out) {

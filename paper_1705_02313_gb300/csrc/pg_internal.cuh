@@ -27,6 +27,7 @@ constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered sca
 // flags[v]
 constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
 constexpr uint8_t kPriOdd = 2;     // priority is odd
+constexpr uint8_t kSinkSlot = 4;   // the id is a game's sink slot, not a vertex
 
 // cls[v]
 constexpr uint8_t kFin = 0;
@@ -34,18 +35,22 @@ constexpr uint8_t kTop = 1;
 constexpr uint8_t kOddCycle = 2;
 
 // Packed nearest-greater-ancestor word gd[v]:
-//   bits 0..31  ptr  (a vertex id, the sink id n, or for "none" vertices the id of the cycle maximum)
-//   bits 32..61 dist (number of steps from v to ptr along the successor function)
+//   bits 0..31  ptr  (a vertex id, the game's sink slot, or for "none" vertices the id of the cycle maximum)
+//   bits 32..60 dist (number of steps from v to ptr along the successor function)
+//   bit  61     sink (ptr is the game's sink slot)
 //   bit  62     none (v is above every vertex of its infinite future)
 //   bit  63     resolved (ptr is final; otherwise ptr is a jump pointer: every vertex strictly between v and ptr is below v)
 constexpr uint64_t kResolved = 1ull << 63;
 constexpr uint64_t kNone = 1ull << 62;
-__host__ __device__ inline uint64_t gd_pack(bool resolved, bool none, uint32_t dist, int32_t ptr) {
-    return (resolved ? kResolved : 0ull) | (none ? kNone : 0ull) | ((uint64_t)(dist & 0x3fffffffu) << 32) |
-           (uint64_t)(uint32_t)ptr;
+constexpr uint64_t kSinkBit = 1ull << 61;
+constexpr uint32_t kDistMax = 0x1fffffffu;
+__host__ __device__ inline uint64_t gd_pack(bool resolved, bool none, uint32_t dist, int32_t ptr, bool sink = false) {
+    return (resolved ? kResolved : 0ull) | (none ? kNone : 0ull) | (sink ? kSinkBit : 0ull) |
+           ((uint64_t)(dist & kDistMax) << 32) | (uint64_t)(uint32_t)ptr;
 }
 __host__ __device__ inline int32_t gd_ptr(uint64_t w) { return (int32_t)(uint32_t)(w & 0xffffffffull); }
-__host__ __device__ inline uint32_t gd_dist(uint64_t w) { return (uint32_t)((w >> 32) & 0x3fffffffu); }
+__host__ __device__ inline uint32_t gd_dist(uint64_t w) { return (uint32_t)((w >> 32) & kDistMax); }
+__host__ __device__ inline bool gd_sink(uint64_t w) { return (w & kSinkBit) != 0; }
 __host__ __device__ inline bool gd_resolved(uint64_t w) { return (w & kResolved) != 0; }
 __host__ __device__ inline bool gd_none(uint64_t w) { return (w & kNone) != 0; }
 
@@ -53,17 +58,17 @@ __host__ __device__ inline bool gd_none(uint64_t w) { return (w & kNone) != 0; }
 constexpr uint8_t kKindFin = 1;        // finite valuation
 constexpr uint8_t kKindSinkChild = 2;  // nearest greater ancestor is the sink
 
-// Device counters of one game (reset at the start of every valuation).
+// Device counters of one valuation (reset at its start).
 struct Counters {
     int32_t n_pending;   // walks that ran out of steps (length of the pending list)
-    int32_t left[2];     // pending vertices left after a jump round (alternating)
+    int32_t left[3];     // pending vertices left after a jump round (three rotating counters)
     int32_t n_fin;       // finite vertices
-    int32_t n_odd;       // vertices reaching an odd cycle
+    int32_t n_odd;       // vertices reaching an odd cycle (all games)
     int32_t n_huge;      // parents ranked by the id-ordered scan
     int32_t n_big;       // parents ranked by one block each
-    int32_t n_switch;    // switched vertices in the last switching pass
+    int32_t n_switch;    // switched vertices in the last switching pass (all games)
     int32_t err;         // device-side error bits (kErr*)
-    int32_t sink_rank;   // rank of the sink's empty valuation
+    int32_t sink_rank;   // rank of game 0's sink (its empty valuation)
     uint32_t bar_count;  // software grid barrier
     uint32_t bar_gen;
     int32_t jump_rounds;
@@ -112,24 +117,50 @@ struct pg_ctx {
     bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
 };
 
+// Per-game state of Algorithm 1 on the device (one entry per game of a batch).
+namespace pg {
+struct GameState {
+    int32_t phase;    // kPhaseActive, kPhaseDone, kPhaseOddCycle, kPhaseTimeout
+    int32_t sw_odd;   // Odd switches in this iteration
+    int32_t sw_even;  // Even switches in this iteration
+    int32_t nodd;     // vertices reaching an odd cycle in this iteration's valuation
+    int64_t inner;    // valuations computed
+    int64_t major;    // Even switching rounds that switched something
+};
+constexpr int32_t kPhaseActive = 0, kPhaseDone = 1, kPhaseOddCycle = 2, kPhaseTimeout = 3;
+}  // namespace pg
+
+// A loaded game, or a batch of games packed into one id space. Every game's
+// relabelled G' vertices occupy a contiguous id range followed by one "sink
+// slot" id that stands for that game's sink (greater than every vertex of the
+// game, as the nearest-greater walks need). A single game is a batch of one.
 struct pg_game {
     pg_ctx* ctx = nullptr;
-    int32_t n0 = 0;   // original vertex count
-    int64_t m0 = 0;   // original edge count
-    int32_t k = 0;    // dummies
-    int32_t n = 0;    // n' = n0 + k
-    int64_t m = 0;    // m' = m0 + k
-    // relabelled G'
-    int32_t* off = nullptr;      // [n+1]
+    int32_t ngames = 1;
+    int64_t n0 = 0;   // original vertices, all games
+    int64_t m0 = 0;   // original edges, all games
+    int32_t k = 0;    // dummies, all games
+    int32_t n = 0;    // ids: G' vertices of all games plus one sink slot per game
+    int64_t m = 0;    // edges of all G'
+    int32_t sink0 = 0;           // the sink slot of game 0 (the only one for a single game)
+    // packed relabelled G'
+    int32_t* off = nullptr;      // [n+1] int32 edge offsets (when m < 2^31), else off64
+    int64_t* off64 = nullptr;    // [n+1]
     int32_t* tgt = nullptr;      // [m]
-    uint8_t* flags = nullptr;    // [n]
-    int32_t* pri = nullptr;      // [n] priority in G'
-    int32_t* nid0 = nullptr;     // [n0] original vertex -> relabelled id
-    int32_t* orig_of = nullptr;  // [n] relabelled id -> original vertex (a dummy reports the vertex it guards)
-    int32_t* dnid = nullptr;     // [k] dummy j -> relabelled id
-    int32_t* dummy_of = nullptr; // [k] dummy j -> original vertex it guards (device)
+    uint8_t* flags = nullptr;    // [n] owner, priority parity, sink slot
+    int32_t* pri = nullptr;      // [n] priority in G' (-1 for sink slots)
+    int32_t* nid0 = nullptr;     // [n0] packed original vertex -> id
+    int32_t* orig_of = nullptr;  // [n] id -> original vertex within its game (a dummy reports the vertex it guards)
+    int32_t* dnid = nullptr;     // [k] packed dummy index -> id
+    int32_t* dummy_of = nullptr; // [k] packed dummy index -> original vertex it guards, within its game
+    int32_t* vgame = nullptr;    // [n] game of each id; nullptr for a single game
+    int32_t* gsink = nullptr;    // [ngames] sink slot id of each game
+    pg::GameState* gst = nullptr;// [ngames]
+    int32_t* gactive = nullptr;  // [1] active games after the last bookkeeping pass
+    std::vector<int64_t> h_base0;  // host: original vertex base of each game (ngames + 1)
+    std::vector<int32_t> h_dbase;  // host: dummy base of each game (ngames + 1)
     // solver state
-    int32_t* strat = nullptr;    // [n] successor under the current profile; n = the sink
+    int32_t* strat = nullptr;    // [n] successor under the current profile (a sink slot for the sink)
     // per-valuation scratch
     uint64_t* gd = nullptr;      // [n] nearest-greater words (pointer, walk length, flags)
     uint32_t* gd32 = nullptr;    // [n] compact g-words read by the chain passes
@@ -139,17 +170,18 @@ struct pg_game {
     int32_t* ccnt = nullptr;     // [n+1] children per parent (zero between valuations)
     int32_t* coff = nullptr;     // [n+2] children segment offsets
     int2* cl_ks = nullptr;       // [n] per child slot: (order key, subtree size)
-    int32_t* sz = nullptr;       // [n] proper descendants in the g-forest (zero between valuations)
+    int32_t* sz = nullptr;       // [n] proper descendants in the g-forest
     int32_t* sinkval = nullptr;  // [n] sink children: subtree size | odd << 31; 0 otherwise
     int32_t* wgt = nullptr;      // [n] chain weight: [even] + sizes of siblings ordered before
-    int32_t* oddsz = nullptr;    // [n] sizes of odd children (zero between valuations)
-    int32_t* key = nullptr;      // [n+1] rank; INT32_MAX for TOP; key[n] = sink rank
+    int32_t* oddsz = nullptr;    // [n] sizes of odd children
+    int32_t* key = nullptr;      // [n] rank; INT32_MAX for TOP; a sink slot holds its sink's rank
     uint8_t* cls = nullptr;      // [n]
     int32_t* depth = nullptr;    // [n]
     int32_t* dom = nullptr;      // [n] dominant priority of the cycle reached (TOP), -1 finite
     int32_t* hugelist = nullptr; // [n] parents with more than kHugeChildren children
-    int64_t* tiles = nullptr;    // [2 * ntiles + 2] cooperative scan tile sums
+    int64_t* tiles = nullptr;    // [2 * ntiles + 2] id-ordered scan tile sums
     int64_t ntiles = 0;
+    int64_t* gscan = nullptr;    // [3 * ngames] per game: even and odd prefix at its first id, odd prefix at its sink
     pg::Counters* cnt = nullptr; // device counters
     pg::Counters* hcnt = nullptr;// pinned host copy
     void* scan_tmp = nullptr;    // children-count scan scratch
@@ -175,6 +207,12 @@ pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where);
 pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const int32_t* tgt,
                     const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out);
 pg_status alloc_scratch(pg_game* g);
+// Packs loaded single games (freed by the call) into one batch game.
+pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out);
+// Per-game loop bookkeeping after the switching passes; counts active games.
+pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase);
+// Resets the per-game state for a new solve.
+pg_status reset_games(pg_game* g);
 void free_game(pg_game* g);
 // Co-resident blocks of the cooperative valuation kernels on a device.
 pg_status coop_blocks_for(pg_ctx* ctx, int* out);

@@ -84,17 +84,27 @@ __device__ inline uint64_t ld_cg(const uint64_t* p) { return __ldcg((const unsig
 __device__ inline void st_cg(uint64_t* p, uint64_t v) { __stcg((unsigned long long*)p, (unsigned long long)v); }
 
 // Compact g-word read by every chain pass: bit 31 = "none" (v is above its
-// whole infinite future; the low bits then name the cycle maximum), low 30
-// bits = g(v) (a vertex or the sink id n; n < 2^30).
+// whole infinite future; the low bits then name the cycle maximum), bit 30 =
+// g(v) is the game's sink, low 30 bits = g(v) (ids < 2^30).
 constexpr uint32_t kG32None = 0x80000000u;
-__device__ inline uint32_t g32_of(uint64_t w) { return (gd_none(w) ? kG32None : 0u) | (uint32_t)gd_ptr(w); }
+constexpr uint32_t kG32Sink = 0x40000000u;
+__device__ inline uint32_t g32_of(uint64_t w) {
+    return (gd_none(w) ? kG32None : 0u) | (gd_sink(w) ? kG32Sink : 0u) | (uint32_t)gd_ptr(w);
+}
 __device__ inline bool g32_none(uint32_t w) { return (w & kG32None) != 0; }
+__device__ inline bool g32_sink(uint32_t w) { return (w & kG32Sink) != 0; }
 __device__ inline int32_t g32_ptr(uint32_t w) { return (int32_t)(w & 0x3fffffffu); }
+
+// The sink slot of v's game.
+__device__ inline int32_t sink_of(int32_t v, const int32_t* vgame, const int32_t* gsink, int32_t sink0) {
+    return vgame ? gsink[vgame[v]] : sink0;
+}
 
 // kind[v], written by k_chain1
 constexpr uint8_t kKFin = 1;        // finite valuation
 constexpr uint8_t kKSinkChild = 2;  // g(v) is the sink
 constexpr uint8_t kKOdd = 4;        // odd priority
+constexpr uint8_t kKSinkSlot = 8;   // the id is a sink slot
 
 // Software grid barrier for cooperative launches (all blocks co-resident).
 // Gives up after a bounded number of spins, records kErrBarrier and returns
@@ -142,6 +152,8 @@ __device__ inline int64_t warp_tile_base(int64_t tile) { return tile * 32 * kIlp
 // kWalkCap steps. A walk that returns to its start found the maximum of its
 // cycle; a walk that runs out of steps leaves a jump pointer for k_jump_coop.
 __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __restrict__ strat,
+                                                 const uint8_t* __restrict__ flags, const int32_t* __restrict__ vgame,
+                                                 const int32_t* __restrict__ gsink, int32_t sink0,
                                                  uint64_t* __restrict__ gd, uint32_t* __restrict__ gd32,
                                                  int32_t* __restrict__ plist, int32_t* __restrict__ sz,
                                                  int32_t* __restrict__ oddsz, Counters* cnt) {
@@ -151,15 +163,16 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
          tile += nwarps) {
         int32_t v[kIlp], x[kIlp];
         uint32_t d[kIlp];
-        bool act[kIlp];
+        bool act[kIlp], slotid[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
-            x[j] = v[j] < n ? __ldg(strat + v[j]) : n;
+            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
             d[j] = 1;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
+        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
         for (;;) {
             bool any = false;
             int32_t nx[kIlp];
@@ -181,7 +194,9 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
             bool pend = false;
             if (v[j] < n) {
                 uint64_t w;
-                if (x[j] > v[j]) w = gd_pack(true, false, d[j], x[j]);       // a larger vertex or the sink
+                if (slotid[j]) w = gd_pack(true, false, 0, v[j], true);  // a sink slot: inert
+                else if (x[j] > v[j])                                     // a larger vertex or the sink
+                    w = gd_pack(true, false, d[j], x[j], x[j] == sink_of(v[j], vgame, gsink, sink0));
                 else if (x[j] == v[j]) w = gd_pack(true, true, d[j], v[j]);  // v is the maximum of its cycle
                 else {
                     w = gd_pack(false, false, d[j], x[j]);
@@ -206,7 +221,9 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
 // Three rotating counters keep each round's count stable until every block
 // has read it.
 __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict__ plist, uint64_t* gd,
-                                                      uint32_t* gd32, Counters* cnt, int32_t cap) {
+                                                      uint32_t* gd32, const int32_t* __restrict__ vgame,
+                                                      const int32_t* __restrict__ gsink, int32_t sink0, Counters* cnt,
+                                                      int32_t cap) {
     const int32_t np = cnt->n_pending;
     if (np == 0) return;
     for (int32_t r = 0;; ++r) {
@@ -225,9 +242,9 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
             } else {
                 int32_t y = gd_ptr(wx);
                 uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
-                if (nd > 0x3fffffffull) nd = 0x3fffffffull;  // only reachable around cycles, where dist is unused
+                if (nd > kDistMax) nd = kDistMax;  // only reachable around cycles, where dist is unused
                 if (y > v) {
-                    nw = gd_pack(true, false, (uint32_t)nd, y);
+                    nw = gd_pack(true, false, (uint32_t)nd, y, y == sink_of(v, vgame, gsink, sink0));
                 } else if (y == v) {
                     nw = gd_pack(true, true, (uint32_t)nd, v);
                 } else {
@@ -262,22 +279,25 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
                                                    const uint8_t* __restrict__ flags, const int32_t* __restrict__ pri,
                                                    int32_t* sz, int32_t* ccnt, int32_t* __restrict__ slot,
                                                    uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
-                                                   int32_t* __restrict__ dom, int want_dom, Counters* cnt) {
+                                                   int32_t* __restrict__ dom, int want_dom,
+                                                   const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t nfin = 0, nodd = 0;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
          tile += nwarps) {
         int32_t v[kIlp], g[kIlp], x[kIlp], cyc[kIlp];
-        bool act[kIlp];
+        bool act[kIlp], sinkchild[kIlp], slotid[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
-            const uint32_t w = v[j] < n ? gd32[v[j]] : (uint32_t)n;
+            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            const uint32_t w = (v[j] < n && !slotid[j]) ? gd32[v[j]] : kG32Sink;
             g[j] = g32_ptr(w);
+            sinkchild[j] = g32_sink(w);
             cyc[j] = g32_none(w) ? g[j] : -1;
             x[j] = g[j];
-            act[j] = v[j] < n && !g32_none(w) && g[j] != n;
+            act[j] = v[j] < n && !slotid[j] && !g32_none(w) && !sinkchild[j];
         }
         // classification walks
         for (;;) {
@@ -293,7 +313,7 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
                         act[j] = false;
                     } else {
                         x[j] = g32_ptr(wx[j]);
-                        act[j] = x[j] != n;
+                        act[j] = !g32_sink(wx[j]);
                     }
                 }
                 any |= act[j];
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
         int32_t sl[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            act[j] = v[j] < n && cyc[j] < 0 && g[j] != n;
+            act[j] = v[j] < n && !slotid[j] && cyc[j] < 0 && !sinkchild[j];
             sl[j] = act[j] ? atomicAdd(ccnt + g[j], 1) : -1;
             x[j] = g[j];
         }
@@ -320,7 +340,7 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
             for (int j = 0; j < kIlp; ++j) {
                 if (act[j]) {
                     x[j] = g32_ptr(wx[j]);
-                    act[j] = x[j] != n;
+                    act[j] = !g32_sink(wx[j]);
                 }
                 any |= act[j];
             }
@@ -329,9 +349,13 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             if (v[j] >= n) continue;
-            if (cyc[j] < 0) {
+            if (slotid[j]) {
+                kind[v[j]] = kKSinkSlot;
+                cls[v[j]] = kFin;
+                if (want_dom) dom[v[j]] = -1;
+            } else if (cyc[j] < 0) {
                 const bool odd_v = (flags[v[j]] & kPriOdd) != 0;
-                kind[v[j]] = kKFin | (g[j] == n ? kKSinkChild : 0) | (odd_v ? kKOdd : 0);
+                kind[v[j]] = kKFin | (sinkchild[j] ? kKSinkChild : 0) | (odd_v ? kKOdd : 0);
                 cls[v[j]] = kFin;
                 if (want_dom) dom[v[j]] = -1;
                 ++nfin;
@@ -340,7 +364,10 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
                 kind[v[j]] = 0;
                 cls[v[j]] = odd ? kOddCycle : kTop;
                 if (want_dom) dom[v[j]] = pri[cyc[j]];
-                nodd += odd;
+                if (odd) {
+                    ++nodd;
+                    atomicAdd(&gst[vgame ? vgame[v[j]] : 0].nodd, 1);
+                }
             }
             slot[v[j]] = sl[j];
         }
@@ -652,9 +679,57 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* tiles,
     }
 }
 
+// Per game g (one warp each): the even and odd exclusive prefixes over all ids
+// at the game's first id and the odd prefix at its sink slot, from the
+// scanned tile sums plus the partial tile. The game's ranks are these global
+// prefixes minus the values at its first id; its sink's rank is its odd total,
+// written into the sink slot's key.
+__device__ inline void prefix_at(int64_t p, int32_t n, const int32_t* __restrict__ sinkval,
+                                 const int64_t* __restrict__ tiles, int64_t* pe, int64_t* po) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = p / kCoopTile;
+    int64_t e = 0, o = 0;
+    for (int64_t i = t * kCoopTile + lane; i < p && i < n; i += 32) {
+        int32_t ee, oo;
+        sink_contrib(sinkval[i], &ee, &oo);
+        e += ee;
+        o += oo;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        e += __shfl_down_sync(kFull, e, d);
+        o += __shfl_down_sync(kFull, o, d);
+    }
+    *pe = tiles[2 * t] + e;
+    *po = tiles[2 * t + 1] + o;
+}
+
+__global__ void __launch_bounds__(kBlock) k_game_prefix(int32_t n, int32_t ngames, const int32_t* __restrict__ gsink,
+                                                        const int32_t* __restrict__ sinkval,
+                                                        const int64_t* __restrict__ tiles, int64_t* gscan,
+                                                        int32_t* key, Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ngames; gi += nw) {
+        const int64_t base = gi == 0 ? 0 : (int64_t)gsink[gi - 1] + 1;
+        const int64_t sk = gsink[gi];
+        int64_t eb, ob, es, os;
+        prefix_at(base, n, sinkval, tiles, &eb, &ob);
+        prefix_at(sk, n, sinkval, tiles, &es, &os);
+        if (lane == 0) {
+            gscan[3 * gi] = eb;
+            gscan[3 * gi + 1] = ob;
+            gscan[3 * gi + 2] = os;
+            key[sk] = (int32_t)(os - ob);
+            if (gi == 0) cnt->sink_rank = (int32_t)(os - ob);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_sink_apply(int32_t n, const int32_t* __restrict__ sinkval,
-                                                       const int64_t* __restrict__ tiles, int64_t ntiles,
-                                                       int32_t* __restrict__ wgt, Counters* cnt) {
+                                                       const int64_t* __restrict__ tiles,
+                                                       const int32_t* __restrict__ vgame,
+                                                       const int64_t* __restrict__ gscan, int32_t* __restrict__ wgt) {
     const int64_t i0 = (int64_t)blockIdx.x * kCoopTile + (int64_t)threadIdx.x * kCIpt;
     int32_t v[kCIpt];
     load8(sinkval, n, i0, v);
@@ -668,16 +743,18 @@ __global__ void __launch_bounds__(kBlock) k_sink_apply(int32_t n, const int32_t*
     }
     int64_t xe, xo, te, to;
     block_scan2(e, o, &xe, &xo, &te, &to);
-    const int64_t tot_o = tiles[2 * ntiles + 1];
     int64_t run_e = tiles[2 * blockIdx.x] + xe, run_o = tiles[2 * blockIdx.x + 1] + xo;
 #pragma unroll
     for (int k = 0; k < kCIpt; ++k) {
-        if (es[k]) wgt[i0 + k] = (int32_t)(1 + tot_o + run_e);
+        if (es[k] | os[k]) {
+            const int64_t gi = vgame ? vgame[i0 + k] : 0;
+            const int64_t eb = gscan[3 * gi], ob = gscan[3 * gi + 1], tot_o = gscan[3 * gi + 2] - ob;
+            if (es[k]) wgt[i0 + k] = (int32_t)(1 + tot_o + (run_e - eb));
+            else wgt[i0 + k] = (int32_t)(tot_o - (run_o + os[k] - ob));
+        }
         run_o += os[k];
-        if (os[k]) wgt[i0 + k] = (int32_t)(tot_o - run_o);
         run_e += es[k];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) cnt->sink_rank = (int32_t)tot_o;
 }
 
 // Parents with more than kHugeChildren children (none in the measured
@@ -767,25 +844,28 @@ __global__ void __launch_bounds__(kBlock) k_idscan_coop(int32_t n, const uint32_
 // rank above everything).
 __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __restrict__ gd32,
                                                    const uint8_t* __restrict__ kind, const int32_t* __restrict__ wgt,
-                                                   const int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
-                                                   const Counters* cnt) {
+                                                   const int32_t* __restrict__ oddsz, int32_t* __restrict__ key) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
          tile += nwarps) {
         int32_t v[kIlp], x[kIlp], acc[kIlp];
-        bool fin[kIlp], act[kIlp];
+        bool fin[kIlp], act[kIlp], slotid[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
-            fin[j] = v[j] < n && (kind[v[j]] & kKFin);
+            const uint8_t kd = v[j] < n ? kind[v[j]] : 0;
+            slotid[j] = (kd & kKSinkSlot) != 0;
+            fin[j] = (kd & kKFin) != 0;
             acc[j] = 0;
-            x[j] = n;
+            x[j] = 0;
+            act[j] = false;
             if (fin[j]) {
                 acc[j] = oddsz[v[j]] + wgt[v[j]];
-                x[j] = g32_ptr(gd32[v[j]]);
+                const uint32_t w = gd32[v[j]];
+                x[j] = g32_ptr(w);
+                act[j] = !g32_sink(w);
             }
-            act[j] = fin[j] && x[j] != n;
         }
         for (;;) {
             bool any = false;
@@ -801,19 +881,16 @@ __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __
                 if (act[j]) {
                     acc[j] += wg[j];
                     x[j] = g32_ptr(wx[j]);
-                    act[j] = x[j] != n;
+                    act[j] = !g32_sink(wx[j]);
                 }
                 any |= act[j];
             }
             if (!any) break;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            if (v[j] >= n) continue;
-            key[v[j]] = fin[j] ? acc[j] : INT32_MAX;
-        }
+        for (int j = 0; j < kIlp; ++j)
+            if (v[j] < n && !slotid[j]) key[v[j]] = fin[j] ? acc[j] : INT32_MAX;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) key[n] = cnt->sink_rank;
 }
 
 // Depth of every finite vertex (outputs only): the number of vertices on its
@@ -825,10 +902,9 @@ __global__ void __launch_bounds__(kBlock) k_depth(int32_t n, const uint64_t* __r
         if (kind[v] & kKFin) {
             uint64_t w = gd[v];
             uint32_t d = gd_dist(w);
-            for (int32_t x = gd_ptr(w); x != n;) {
-                uint64_t wx = gd[x];
-                d += gd_dist(wx);
-                x = gd_ptr(wx);
+            while (!gd_sink(w)) {
+                w = gd[gd_ptr(w)];
+                d += gd_dist(w);
             }
             dep = (int32_t)d;
         }
@@ -839,20 +915,34 @@ __global__ void __launch_bounds__(kBlock) k_depth(int32_t n, const uint64_t* __r
 // K3: greedy all-switches for one player, one thread per vertex. Edges are
 // taken in batches of four whose target reads and rank gathers are issued
 // together, then compared in edge-list order (first minimiser for Odd; for
-// Even the sink first, then the first maximiser).
-__global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const int32_t* __restrict__ off,
+// Even the sink first, then the first maximiser). A game takes part while it
+// is active; Even switches only in games where no Odd vertex switched in this
+// iteration (the inner loop of Algorithm 1 has converged).
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const OffT* __restrict__ off,
                                                    const int32_t* __restrict__ tgt,
                                                    const uint8_t* __restrict__ flags,
-                                                   const int32_t* __restrict__ key, int32_t* strat, Counters* cnt) {
+                                                   const int32_t* __restrict__ key, const int32_t* __restrict__ vgame,
+                                                   const int32_t* __restrict__ gsink, int32_t sink0, GameState* gst,
+                                                   int32_t* strat, Counters* cnt) {
+    if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
+        const GameState st = gst[0];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
+    }
     int32_t nsw = 0;
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if ((int)(flags[v] & kOwnerOdd) != player) continue;
-        const int32_t e0 = off[v], e1 = off[v + 1];
+        const uint8_t f = flags[v];
+        if ((f & kSinkSlot) || (int)(f & kOwnerOdd) != player) continue;
+        const int32_t gi = vgame ? vgame[v] : 0;
+        const GameState st = gst[gi];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) continue;
+        const int64_t e0 = off[v], e1 = off[v + 1];
         const int32_t cur = strat[v];
-        int32_t best = player == 0 ? n : -1;
-        int32_t bk = player == 0 ? key[n] : INT32_MAX;
+        const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : 0;
+        int32_t best = player == 0 ? sk : -1;
+        int32_t bk = player == 0 ? key[sk] : INT32_MAX;
         const int32_t curkey = key[cur];
-        for (int32_t e = e0; e < e1; e += 4) {
+        for (int64_t e = e0; e < e1; e += 4) {
             int32_t t[4], kk[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? tgt[e + j] : -1;
@@ -871,9 +961,45 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
         if (player == 0 ? bk > curkey : bk < curkey) {
             strat[v] = best;
             ++nsw;
+            if (vgame) atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, 1);
         }
     }
     block_add(nsw, &cnt->n_switch);
+    if (!vgame) {  // one game: the block totals are the game's
+        __shared__ int32_t tot;
+        if (threadIdx.x == 0) tot = 0;
+        __syncthreads();
+        int32_t x = nsw;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&tot, x);
+        __syncthreads();
+        if (threadIdx.x == 0 && tot) atomicAdd(player ? &gst[0].sw_odd : &gst[0].sw_even, tot);
+    }
+}
+
+// Per-game bookkeeping of Algorithm 1 after the switching passes (one thread
+// per game): count the valuation, stop at an odd cycle, finish when neither
+// player switched (or, for best responses, when Odd did not), count a major
+// iteration when Even switched, stop at the cap. Counts the games still active.
+__global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even_phase, int32_t* gactive) {
+    int32_t act = 0;
+    for (int32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngames; gi += gridDim.x * blockDim.x) {
+        GameState st = gst[gi];
+        if (st.phase == kPhaseActive) {
+            st.inner += 1;
+            if (st.nodd > 0) st.phase = kPhaseOddCycle;
+            else if (st.sw_odd == 0) {
+                if (!even_phase || st.sw_even == 0) st.phase = kPhaseDone;
+                else st.major += 1;
+            }
+            if (st.phase == kPhaseActive && st.inner >= cap) st.phase = kPhaseTimeout;
+        }
+        st.sw_odd = st.sw_even = st.nodd = 0;
+        gst[gi] = st;
+        act += st.phase == kPhaseActive;
+    }
+    block_add(act, gactive);
 }
 
 }  // namespace
@@ -908,7 +1034,7 @@ void prof_collect(pg_game* g) {
 
 pg_status alloc_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
-    int64_t n = g->n;
+    const int64_t n = g->n;
     auto A = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 1); };
     PG_CUDA_TRY(ctx, A((void**)&g->gd, sizeof(uint64_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->gd32, sizeof(uint32_t) * n));
@@ -922,23 +1048,22 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A((void**)&g->sinkval, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->wgt, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->oddsz, sizeof(int32_t) * n));
-    PG_CUDA_TRY(ctx, A((void**)&g->key, sizeof(int32_t) * (n + 1)));
+    PG_CUDA_TRY(ctx, A((void**)&g->key, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->cls, n));
     PG_CUDA_TRY(ctx, A((void**)&g->depth, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->dom, sizeof(int32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->hugelist, sizeof(int32_t) * n));
     g->ntiles = std::max<int64_t>(1, (n + kCoopTile - 1) / kCoopTile);
     PG_CUDA_TRY(ctx, A((void**)&g->tiles, sizeof(int64_t) * (2 * g->ntiles + 2)));
+    PG_CUDA_TRY(ctx, A((void**)&g->gscan, sizeof(int64_t) * 3 * (size_t)g->ngames));
+    PG_CUDA_TRY(ctx, A((void**)&g->gst, sizeof(GameState) * (size_t)g->ngames));
+    PG_CUDA_TRY(ctx, A((void**)&g->gactive, sizeof(int32_t)));
     PG_CUDA_TRY(ctx, A((void**)&g->cnt, sizeof(Counters)));
     PG_CUDA_TRY(ctx, cudaMallocHost((void**)&g->hcnt, sizeof(Counters)));
     g->scan_tmp_bytes = scan_tmp_bytes(n + 2) + 64;
     PG_CUDA_TRY(ctx, A(&g->scan_tmp, g->scan_tmp_bytes));
-    // co-resident blocks for the cooperative kernels
-    int sms = 0, a = 0, b = 0;
-    PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump_coop, kBlock, 0));
-    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_idscan_coop, kBlock, 0));
-    g->coop_blocks = sms * std::max(1, std::min(std::min(a, b), 4));
+    pg_status st = coop_blocks_for(ctx, &g->coop_blocks);
+    if (st) return st;
     for (int i = 0; i < 4; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->ev[i]));
     for (int i = 0; i < 2 * KID_COUNT; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->kev[i]));
     return reset_scratch(g);
@@ -956,10 +1081,16 @@ pg_status coop_blocks_for(pg_ctx* ctx, int* out) {
 pg_status reset_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
-    int64_t n = g->n;
+    const int64_t n = g->n;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->oddsz, 0, sizeof(int32_t) * n, s));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->ccnt, 0, sizeof(int32_t) * (n + 1), s));
+    return reset_games(g);
+}
+
+pg_status reset_games(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gst, 0, sizeof(GameState) * (size_t)g->ngames, ctx->stream));
     return PG_OK;
 }
 
@@ -971,19 +1102,21 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     const unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->gd, g->gd32, g->plist, g->sz, g->oddsz, c);
+    k_walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd, g->gd32,
+                                          g->plist, g->sz, g->oddsz, c);
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
-        void* args[] = {(void*)&g->plist, (void*)&g->gd, (void*)&g->gd32, (void*)&c, (void*)&cap};
+        void* args[] = {(void*)&g->plist, (void*)&g->gd,    (void*)&g->gd32, (void*)&g->vgame,
+                        (void*)&g->gsink, (void*)&g->sink0, (void*)&c,       (void*)&cap};
         prof_begin(g, KID_JUMP);
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
         prof_end(g, KID_JUMP, 1);
     }
     prof_begin(g, KID_CHAIN1);
-    k_chain1<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls, g->dom,
-                                     want_dom ? 1 : 0, c);
+    k_chain1<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls,
+                                            g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c);
     prof_end(g, KID_CHAIN1, 1);
     prof_begin(g, KID_CSCAN);
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
@@ -1003,11 +1136,13 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_idscan_coop, g->coop_blocks, kBlock, args, 0, s));
         k_sink_reduce<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles);
         k_tiles_scan<<<1, kTileScanThreads, 0, s>>>(g->tiles, g->ntiles);
-        k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->ntiles, g->wgt, c);
+        const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + 7) / 8, 4096));
+        k_game_prefix<<<gp, kBlock, 0, s>>>(n, g->ngames, g->gsink, g->sinkval, g->tiles, g->gscan, g->key, c);
+        k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->vgame, g->gscan, g->wgt);
     }
-    prof_end(g, KID_SINKSCAN, 4);
+    prof_end(g, KID_SINKSCAN, 5);
     prof_begin(g, KID_CHAIN2);
-    k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key, c);
+    k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key);
     prof_end(g, KID_CHAIN2, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
@@ -1027,8 +1162,24 @@ pg_status enqueue_switch(pg_game* g, int player) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
     int kid = player ? KID_SWITCH_ODD : KID_SWITCH_EVEN;
     prof_begin(g, kid);
-    k_switch<<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->key, g->strat, g->cnt);
+    if (g->off64)
+        k_switch<int64_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off64, g->tgt, g->flags, g->key, g->vgame,
+                                                            g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+    else
+        k_switch<int32_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->key, g->vgame,
+                                                            g->gsink, g->sink0, g->gst, g->strat, g->cnt);
     prof_end(g, kid, 1);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gactive, 0, sizeof(int32_t), s));
+    ctx->launches += 1;
+    const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + kBlock - 1) / kBlock, 1024));
+    k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->gactive);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }

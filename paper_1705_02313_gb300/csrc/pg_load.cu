@@ -199,7 +199,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     *out = nullptr;
     if (!off_in || !tgt_in || !own_in || !pri_in) return fail(ctx, PG_EINVAL, "pg_load_csr: NULL array");
     if (mem_kind != PG_MEM_HOST && mem_kind != PG_MEM_DEVICE) return fail(ctx, PG_EINVAL, "pg_load_csr: bad mem_kind");
-    if (n < 1 || n >= (1 << 30)) return fail(ctx, PG_EINVAL, "pg_load_csr: n must be in [1, 2^30)");
+    if (n < 1 || n >= (1 << 29)) return fail(ctx, PG_EINVAL, "pg_load_csr: n must be in [1, 2^29)");
     if (m < n || m > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: m must be in [n, 2^31-1)");
     cudaStream_t s = ctx->stream;
     cudaMemcpyKind kind = mem_kind == PG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -296,7 +296,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(&k, widx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     int64_t np = (int64_t)n + k, mp = m + k;
-    if (np >= (1 << 30)) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^30 vertices after preprocessing");
+    if (np >= (1 << 29) - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^29 vertices after preprocessing");
     if (mp > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^31-2 edges after preprocessing");
     if ((int64_t)maxpri + 2 * (int64_t)k > INT32_MAX - 1)
         return fail(ctx, PG_EINVAL, "pg_load_csr: priorities too large for the preprocessing shift");
@@ -306,8 +306,12 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     g->n0 = n;
     g->m0 = m;
     g->k = k;
-    g->n = (int32_t)np;
+    g->n = (int32_t)np + 1;  // G' vertices and the sink slot
     g->m = mp;
+    g->sink0 = (int32_t)np;
+    g->ngames = 1;
+    g->h_base0 = {0, (int64_t)n};
+    g->h_dbase = {0, k};
     auto bail = [&](cudaError_t e, const char* where) {
         free_game(g);
         return cuda_fail(ctx, e, where);
@@ -317,15 +321,16 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         cudaError_t _e = (expr);                      \
         if (_e != cudaSuccess) return bail(_e, #expr); \
     } while (0)
-    LG_TRY(dalloc(&g->off, np + 1));
+    LG_TRY(dalloc(&g->off, np + 2));
     LG_TRY(dalloc(&g->tgt, mp));
-    LG_TRY(dalloc(&g->flags, np));
-    LG_TRY(dalloc(&g->pri, np));
+    LG_TRY(dalloc(&g->flags, np + 1));
+    LG_TRY(dalloc(&g->pri, np + 1));
     LG_TRY(dalloc(&g->nid0, n));
-    LG_TRY(dalloc(&g->orig_of, np));
+    LG_TRY(dalloc(&g->orig_of, np + 1));
     LG_TRY(dalloc(&g->dnid, k));
     LG_TRY(dalloc(&g->dummy_of, k));
-    LG_TRY(dalloc(&g->strat, np));
+    LG_TRY(dalloc(&g->strat, np + 1));
+    LG_TRY(dalloc(&g->gsink, 1));
     ++ctx->launches;
     k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
 
@@ -359,6 +364,17 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
                                                   gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of);
     ++ctx->launches;
     k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
+    // the sink slot: no edges, a flag, no priority or original vertex
+    {
+        const int32_t sk = (int32_t)np;
+        const uint8_t sf = kSinkSlot;
+        LG_TRY(cudaMemcpyAsync(g->off + np + 1, g->off + np, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        LG_TRY(cudaMemcpyAsync(g->flags + np, &sf, 1, cudaMemcpyHostToDevice, s));
+        LG_TRY(cudaMemsetAsync(g->pri + np, 0xff, sizeof(int32_t), s));
+        LG_TRY(cudaMemsetAsync(g->orig_of + np, 0xff, sizeof(int32_t), s));
+        LG_TRY(cudaMemcpyAsync(g->strat + np, &sk, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        LG_TRY(cudaMemcpyAsync(g->gsink, &sk, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
     LG_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
     LG_TRY(cudaStreamSynchronize(s));
     LG_TRY(cudaGetLastError());

@@ -25,11 +25,11 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the arrays inside the static buffer, for kStaticMaxN vertices.
 struct Layout {
     size_t gd, gd32, plist, slot, ccnt, coff, cl_ks, sz, sinkval, wgt, oddsz, key, cls, kind, depth, hugelist,
-        flags, tiles, cnt, scan, bytes;
+        flags, tiles, gst, gscan, gsink, cnt, scan, bytes;
 };
 
 constexpr Layout make_layout() {
-    const size_t N = kStaticMaxN;
+    const size_t N = kStaticMaxN + 1;  // the vertices and the sink slot
     const size_t ntiles = (N + kCoopTile - 1) / kCoopTile;
     Layout L{};
     size_t p = 0;
@@ -51,6 +51,9 @@ constexpr Layout make_layout() {
     L.hugelist = p; p = al256(p + 4 * N);
     L.flags = p;    p = al256(p + N);
     L.tiles = p;    p = al256(p + 8 * (2 * ntiles + 2));
+    L.gst = p;      p = al256(p + sizeof(GameState));
+    L.gscan = p;    p = al256(p + 3 * 8);
+    L.gsink = p;    p = al256(p + 4);
     L.cnt = p;      p = al256(p + sizeof(Counters));
     L.scan = p;     p = al256(p + 8 * ((N + 2 + 2047) / 2048 + 2) + 64);
     L.bytes = p;
@@ -68,10 +71,15 @@ int g_static_coop[kMaxDevices] = {};
 std::mutex g_static_mu;
 Counters g_static_hcnt;  // host copy of the counters (pageable, fixed)
 
-// flags and range check: succ must be in [0, n]
+// flags and range check: succ must be in [0, n]; id n is the sink slot
 __global__ void k_static_prepare(int32_t n, const int32_t* __restrict__ succ, const uint8_t* __restrict__ odd,
-                                 uint8_t* __restrict__ flags, Counters* cnt) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+                                 uint8_t* __restrict__ flags, int32_t* gsink, Counters* cnt) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        if (v == n) {
+            flags[v] = kSinkSlot;
+            *gsink = n;
+            continue;
+        }
         const int32_t s = succ[v];
         if (s < 0 || s > n) atomicOr(&cnt->err, 1);
         flags[v] = odd[v] ? kPriOdd : 0;
@@ -131,8 +139,10 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     // a game view over the static buffer: only the fields the valuation reads
     pg_game g;
     g.ctx = &ctx;
-    g.n = n;
-    g.strat = const_cast<int32_t*>(succ);  // read only by the valuation
+    g.n = n + 1;  // the vertices and the sink slot
+    g.sink0 = n;
+    g.ngames = 1;
+    g.strat = const_cast<int32_t*>(succ);  // read only by the valuation, never at the sink slot
     g.gd = (uint64_t*)(base + kLayout.gd);
     g.gd32 = (uint32_t*)(base + kLayout.gd32);
     g.plist = (int32_t*)(base + kLayout.plist);
@@ -151,7 +161,10 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     g.hugelist = (int32_t*)(base + kLayout.hugelist);
     g.flags = (uint8_t*)(base + kLayout.flags);
     g.tiles = (int64_t*)(base + kLayout.tiles);
-    g.ntiles = std::max<int64_t>(1, ((int64_t)n + kCoopTile - 1) / kCoopTile);
+    g.ntiles = std::max<int64_t>(1, ((int64_t)n + 1 + kCoopTile - 1) / kCoopTile);
+    g.gst = (GameState*)(base + kLayout.gst);
+    g.gscan = (int64_t*)(base + kLayout.gscan);
+    g.gsink = (int32_t*)(base + kLayout.gsink);
     g.cnt = (Counters*)(base + kLayout.cnt);
     g.hcnt = &g_static_hcnt;
     g.scan_tmp = base + kLayout.scan;
@@ -160,8 +173,8 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
 
     cudaStream_t s = ctx.stream;
     if (cudaMemsetAsync(g.cnt, 0, sizeof(Counters), s) != cudaSuccess) return PG_ECUDA;
-    k_static_prepare<<<(unsigned)std::min<int64_t>(((int64_t)n + kBlock - 1) / kBlock, 4096), kBlock, 0, s>>>(
-        n, succ, odd, g.flags, g.cnt);
+    k_static_prepare<<<(unsigned)std::min<int64_t>(((int64_t)n + kBlock) / kBlock, 4096), kBlock, 0, s>>>(
+        n, succ, odd, g.flags, g.gsink, g.cnt);
     if (cudaMemcpyAsync(&g_static_hcnt, g.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return PG_ECUDA;
