@@ -172,6 +172,45 @@ pg_status pg_reset_stats(pg_game *game);
 /* Number of kernels launched through ctx since it was created. */
 pg_status pg_launch_count(const pg_ctx *ctx, int64_t *out);
 
+/* Results of a batch (pg_solve_batch). Per-vertex arrays are packed like the
+ * inputs (game i's vertices at vtx_base[i] .. vtx_base[i+1]) and hold that
+ * game's local vertex ids; NULL skips an output. dummy_sigma is packed by game
+ * with dummy_base (ngames + 1 entries, host) telling where each game's dummies
+ * start. major, inner and status are host arrays of ngames entries (each
+ * nullable); status is PG_OK, PG_ETIMEOUT or PG_ENOTADMISSIBLE per game. */
+typedef struct {
+    uint8_t *win;
+    int32_t *sigma;
+    int32_t *tau;
+    int8_t *val_class;
+    int32_t *val_depth;
+    int32_t *val_rank;
+    int8_t *dummy_sigma;
+    int32_t mem_kind;      /* where the per-vertex and dummy arrays live */
+    int64_t *major;        /* host, ngames */
+    int64_t *inner;        /* host, ngames */
+    int32_t *status;       /* host, ngames */
+    int64_t *dummy_base;   /* host, ngames + 1, out */
+    int64_t iterations;    /* out: lockstep iterations run for the whole batch */
+} pg_result_batch;
+
+/* Solves many games together (Algorithm 1, Section 4, for each): all games
+ * share one packed id space on the device, every pass runs once over all of
+ * them, and each game keeps its own loop state, so each result is exactly the
+ * one pg_solve gives for that game alone. Inputs are packed: game i has
+ * vertices vtx_base[i] .. vtx_base[i+1] of owner and pri, edges
+ * edge_base[i] .. edge_base[i+1] of targets (local vertex ids of the game),
+ * and n_i + 1 local CSR offsets starting at offsets[vtx_base[i] + i].
+ * vtx_base and edge_base are host arrays of ngames + 1 entries starting at 0;
+ * the other inputs use mem_kind. Each game is validated and preprocessed as in
+ * pg_load_csr (same errors); the batch may hold up to 2^30 vertices after
+ * preprocessing and any number of edges. max_inner caps the lockstep
+ * iterations (0 = 64 * (largest game + 64)). Returns PG_ETIMEOUT or
+ * PG_ENOTADMISSIBLE if any game ended that way (results are still written). */
+pg_status pg_solve_batch(pg_ctx *ctx, int32_t ngames, const int64_t *vtx_base, const int64_t *edge_base,
+                         const int32_t *offsets, const int32_t *targets, const uint8_t *owner, const int32_t *pri,
+                         int32_t mem_kind, int64_t max_inner, pg_result_batch *out);
+
 /* Valuation of one successor function without allocating any memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory themselves or let a library do it, for example code

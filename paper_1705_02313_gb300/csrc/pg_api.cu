@@ -154,6 +154,8 @@ Stage stage_layout(int64_t n0, int64_t k) {
     return s;
 }
 
+}  // namespace
+
 pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
                         int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig) {
     pg_ctx* ctx = g->ctx;
@@ -241,24 +243,7 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
     return PG_OK;
 }
 
-struct Timer {
-    pg_game* g;
-    bool on;
-    explicit Timer(pg_game* gg) : g(gg), on(gg->ctx->timing) {
-        g->t_total = g->t_val = g->t_switch = 0;
-        g->t_vals = 0;
-    }
-    void mark(int i) {
-        if (on) cudaEventRecord(g->ev[i], g->ctx->stream);
-    }
-    double since(int a, int b) {
-        if (!on) return 0;
-        cudaEventSynchronize(g->ev[b]);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, g->ev[a], g->ev[b]);
-        return ms;
-    }
-};
+
 
 // Algorithm 1 for every game of g at once: each iteration computes the
 // valuation of every game, switches Odd in active games, switches Even in
@@ -288,7 +273,6 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
     }
 }
 
-}  // namespace
 }  // namespace pg
 
 using namespace pg;

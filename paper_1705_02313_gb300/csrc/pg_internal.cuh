@@ -205,8 +205,36 @@ namespace pg {
 pg_status fail(pg_ctx* ctx, pg_status code, const char* msg);
 pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where);
 pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const int32_t* tgt,
-                    const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out);
+                    const uint8_t* own, const int32_t* pri, int32_t mem_kind, pg_game** out,
+                    bool with_scratch = true);
 pg_status alloc_scratch(pg_game* g);
+// Event timing of a call's phases (active when the context's timing is on).
+struct Timer {
+    pg_game* g;
+    bool on;
+    explicit Timer(pg_game* gg) : g(gg), on(gg->ctx->timing) {
+        g->t_total = g->t_val = g->t_switch = 0;
+        g->t_vals = 0;
+    }
+    void mark(int i) {
+        if (on) cudaEventRecord(g->ev[i], g->ctx->stream);
+    }
+    double since(int a, int b) {
+        if (!on) return 0;
+        cudaEventSynchronize(g->ev[b]);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, g->ev[a], g->ev[b]);
+        return ms;
+    }
+};
+
+// Sets g->strat from a profile in original ids (NULL arrays: the initial profile).
+pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, const int8_t* dsig, int32_t mem_kind);
+// Writes results in original ids (host or device arrays; NULL skips).
+pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
+                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig);
+// Algorithm 1 for all games of g (even = false: inner loop only).
+pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm);
 // Packs loaded single games (freed by the call) into one batch game.
 pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out);
 // Per-game loop bookkeeping after the switching passes; counts active games.

@@ -194,7 +194,7 @@ struct Temps {
 }  // namespace
 
 pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, const int32_t* tgt_in,
-                    const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out) {
+                    const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out, bool with_scratch) {
     if (!out) return fail(ctx, PG_EINVAL, "pg_load_csr: out is NULL");
     *out = nullptr;
     if (!off_in || !tgt_in || !own_in || !pri_in) return fail(ctx, PG_EINVAL, "pg_load_csr: NULL array");
@@ -383,7 +383,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: internal priority collision after preprocessing");
     }
 #undef LG_TRY
-    pg_status st = alloc_scratch(g);
+    pg_status st = with_scratch ? alloc_scratch(g) : PG_OK;
     if (st != PG_OK) {
         free_game(g);
         return st;

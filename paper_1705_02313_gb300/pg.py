@@ -50,6 +50,13 @@ class pg_valuation(C.Structure):
                 ("dom", C.c_void_p), ("mem_kind", C.c_int32)]
 
 
+class pg_result_batch(C.Structure):
+    _fields_ = [("win", C.c_void_p), ("sigma", C.c_void_p), ("tau", C.c_void_p), ("val_class", C.c_void_p),
+                ("val_depth", C.c_void_p), ("val_rank", C.c_void_p), ("dummy_sigma", C.c_void_p),
+                ("mem_kind", C.c_int32), ("major", C.c_void_p), ("inner", C.c_void_p), ("status", C.c_void_p),
+                ("dummy_base", C.c_void_p), ("iterations", C.c_int64)]
+
+
 class pg_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_double), ("launches", C.c_int64), ("calls", C.c_int64)]
 
@@ -88,10 +95,11 @@ def lib():
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(I64)]
     L.pg_valuate_static.argtypes = [I32, P, P, P, P, P, P]
+    L.pg_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, I32, I64, C.POINTER(pg_result_batch)]
     L.pg_kernel_stats.argtypes = [P, C.POINTER(pg_kernel_stat), I32, C.POINTER(I32)]
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
-    for name in ["pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
+    for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -245,6 +253,48 @@ def pg_valuate(ctx, game, sigma=None, tau=None, dummy_sigma=None, val_class=None
     if rc not in (PG_OK, PG_ENOTADMISSIBLE):
         _check(ctx, rc, "pg_valuate")
     return rc
+
+
+def pg_solve_batch(ctx, ngames, vtx_base, edge_base, offsets, targets, owner, pri, max_inner=0, win=None,
+                   sigma=None, tau=None, val_class=None, val_depth=None, val_rank=None, dummy_sigma=None):
+    """vtx_base, edge_base: int64 numpy arrays (ngames + 1). Returns a dict with
+    per-game major, inner, status (numpy), dummy_base and iterations; the given
+    output arrays are filled."""
+    vtx_base = np.ascontiguousarray(vtx_base, dtype=np.int64)
+    edge_base = np.ascontiguousarray(edge_base, dtype=np.int64)
+    for a, dt, nm in [(offsets, np.int32, "offsets"), (targets, np.int32, "targets"), (owner, np.uint8, "owner"),
+                      (pri, np.int32, "pri")]:
+        _dtype_check(a, dt, nm)
+    kind = _same_kind(offsets, targets, owner, pri)
+    major = np.zeros(ngames, np.int64)
+    inner = np.zeros(ngames, np.int64)
+    status = np.zeros(ngames, np.int32)
+    dbase = np.zeros(ngames + 1, np.int64)
+    res = pg_result_batch(_ptr_kind(win)[0], _ptr_kind(sigma)[0], _ptr_kind(tau)[0], _ptr_kind(val_class)[0],
+                          _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dummy_sigma)[0],
+                          _same_kind(win, sigma, tau, val_class, val_depth, val_rank, dummy_sigma),
+                          major.ctypes.data, inner.ctypes.data, status.ctypes.data, dbase.ctypes.data, 0)
+    rc = lib().pg_solve_batch(ctx, int(ngames), vtx_base.ctypes.data, edge_base.ctypes.data, _ptr_kind(offsets)[0],
+                              _ptr_kind(targets)[0], _ptr_kind(owner)[0], _ptr_kind(pri)[0], kind, int(max_inner),
+                              C.byref(res))
+    if rc not in (PG_OK, PG_ETIMEOUT, PG_ENOTADMISSIBLE):
+        _check(ctx, rc, "pg_solve_batch")
+    return dict(rc=rc, major=major, inner=inner, status=status, dummy_base=dbase, iterations=res.iterations)
+
+
+def pack_games(games):
+    """Packs generator games into the pg_solve_batch input layout (host arrays)."""
+    nv = np.array([g.n for g in games], np.int64)
+    ne = np.array([g.m for g in games], np.int64)
+    vtx_base = np.zeros(len(games) + 1, np.int64)
+    edge_base = np.zeros(len(games) + 1, np.int64)
+    np.cumsum(nv, out=vtx_base[1:])
+    np.cumsum(ne, out=edge_base[1:])
+    offsets = np.concatenate([g.offsets for g in games]).astype(np.int32)
+    targets = np.concatenate([g.targets for g in games]).astype(np.int32)
+    owner = np.concatenate([g.owner for g in games]).astype(np.uint8)
+    pri = np.concatenate([g.pri for g in games]).astype(np.int32)
+    return vtx_base, edge_base, offsets, targets, owner, pri
 
 
 def pg_valuate_static(n, succ, odd, val_class=None, val_depth=None, val_rank=None, stream=None):
