@@ -53,8 +53,8 @@ def make_game(name):
     from paper_1705_02313_gb300 import gen
     fn, kw, _ = WORKLOADS[name]
     kw = dict(kw)
-    if fn == "random_game":
-        return gen.random_game(kw["n"], kw["dmin"], kw["dmax"], kw["seed"])
+    if fn == "random_game":  # the C generator: the same game as gen.random_game
+        return gen.native_random_game(kw["n"], kw["dmin"], kw["dmax"], kw["seed"])
     return gen.ladder_game(kw["n"], kw["seed"])
 
 
@@ -165,6 +165,84 @@ def measured_traffic(kernel, workload):
         return e["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+# ---------------------------------------------------------------------------
+# batches: pg_solve_batch against a loop of pg_load_csr + pg_solve
+
+BATCHES = {
+    # name: (games, size lo, size hi, out-degree lo, hi, description)
+    "batch-256": (256, 1_000, 100_000, 2, 6,
+                  "256 random games, sizes log-uniform in [1e3, 1e5], out-degree U[2,6], owners p=0.5, permuted "
+                  "priorities, game i seeded by SplitMix64(0x5EED ^ i)"),
+    "batch-4096": (4096, 1_000, 1_000_000, 2, 6,
+                   "4,096 random games, sizes log-uniform in [1e3, 1e6], out-degree U[2,6], owners p=0.5, permuted "
+                   "priorities, game i seeded by SplitMix64(0x5EED ^ i)"),
+}
+
+
+def batch_measure(name):
+    """Solves the batch three ways, each once after a warm-up on its first
+    games: pg_solve_batch with the inputs already in device memory, the same
+    from host arrays with results copied back (end to end), and a loop of
+    pg_load_csr + pg_solve over the same games one at a time."""
+    import torch
+
+    from paper_1705_02313_gb300 import gen, pg
+    count, lo, hi, dmin, dmax, desc = BATCHES[name]
+    t0 = time.perf_counter()
+    vb, eb, off, tgt, own, pri = gen.native_batch(count, lo, hi, dmin, dmax)
+    t_gen = time.perf_counter() - t0
+    n0, m0 = int(vb[-1]), int(eb[-1])
+    dev = [torch.from_numpy(a).cuda() for a in (off, tgt, own, pri)]
+    out = dict(win=torch.empty(n0, dtype=torch.uint8, device="cuda"),
+               sigma=torch.empty(n0, dtype=torch.int32, device="cuda"))
+    ctx = pg.pg_ctx_create(0)
+    try:
+        w = min(count, 16)  # warm-up: the first games
+        pg.pg_solve_batch(ctx, w, vb[:w + 1], eb[:w + 1], *dev, **out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pg.pg_solve_batch(ctx, count, vb, eb, *dev, **out)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        win_b = out["win"].cpu().numpy()
+        sig_b = out["sigma"].cpu().numpy()
+        # end to end: host inputs, results back in host memory
+        hwin = np.empty(n0, np.uint8)
+        hsig = np.empty(n0, np.int32)
+        t0 = time.perf_counter()
+        pg.pg_solve_batch(ctx, count, vb, eb, off, tgt, own, pri, win=hwin, sigma=hsig)
+        t_e2e = time.perf_counter() - t0
+        # one game at a time through the single-game entry points
+        o_off, o_tgt, o_own, o_pri = dev
+        t0 = time.perf_counter()
+        inner_sum = 0
+        for i in range(count):
+            a, b = int(vb[i]), int(vb[i + 1])
+            e0, e1 = int(eb[i]), int(eb[i + 1])
+            g = pg.pg_load_csr(ctx, b - a, e1 - e0, o_off[a + i:b + i + 1], o_tgt[e0:e1], o_own[a:b], o_pri[a:b])
+            try:
+                _, inner = pg.pg_solve(ctx, g, win=out["win"][a:b], sigma=out["sigma"][a:b])
+                inner_sum += inner
+            finally:
+                pg.pg_game_free(g)
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t0
+        same = bool(np.array_equal(win_b, out["win"].cpu().numpy()) and np.array_equal(sig_b, out["sigma"].cpu().numpy())
+                    and np.array_equal(win_b, hwin) and np.array_equal(sig_b, hsig))
+    finally:
+        pg.pg_ctx_destroy(ctx)
+    inner = res["inner"]
+    return {"workload": name, "description": desc, "games": count, "vertices": n0, "edges": m0,
+            "metric": "batched games/s vs one-at-a-time", "unit": "games/s",
+            "batched_games_per_s": count / t_batch, "batched_e2e_games_per_s": count / t_e2e,
+            "one_at_a_time_games_per_s": count / t_single, "speedup": t_single / t_batch,
+            "batched_s": t_batch, "batched_e2e_s": t_e2e, "one_at_a_time_s": t_single,
+            "lockstep_iterations": int(res["iterations"]), "inner_min": int(inner.min()),
+            "inner_max": int(inner.max()), "valuations_one_at_a_time": int(inner_sum),
+            "generate_s": t_gen, "identical_results": same,
+            "timing": "wall clock around each call, device synchronised; includes loading and preprocessing"}
 
 
 # ---------------------------------------------------------------------------
@@ -360,6 +438,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if rank == 0 and not args.no_batch:
+        line["batch"] = batch_measure(args.batch)
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_sample(game, args.cpu_iters)
         line["cpu_baseline"] = {"value": r["edges"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -415,6 +495,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-one-at-a-time measurement")
+    ap.add_argument("--batch", choices=sorted(BATCHES), default="batch-256",
+                    help="batch workload measured beside the main line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -1,9 +1,11 @@
-"""Builds libpg.so (the CUDA solver behind include/pg.h) for sm_103a.
+"""Builds libpg.so (the CUDA solver behind include/pg.h) for sm_103a, and
+libpggen.so (the multithreaded host generator of random games).
 
 Each translation unit under csrc/ is compiled in parallel with
 ``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and the objects
 are linked into ``paper_1705_02313_gb300/libpg.so`` (CUDA runtime linked
-statically). Rebuilds only when a source or header is newer than the library.
+statically); ``csrc/gen_host.c`` is compiled by the host C compiler. Each
+library is rebuilt only when one of its sources is newer than it.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpg.so")
+GEN_LIB = os.path.join(HERE, "libpggen.so")
+GEN_SRC = os.path.join(CSRC, "gen_host.c")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
@@ -41,7 +45,23 @@ def _stale():
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+def build_gen(force: bool = False) -> str:
+    """Compiles the host generator (plain C, no CUDA)."""
+    if not force and os.path.exists(GEN_LIB) and os.path.getmtime(GEN_LIB) >= max(
+            os.path.getmtime(GEN_SRC), os.path.getmtime(__file__)):
+        return GEN_LIB
+    cc = os.environ.get("CC", "gcc")
+    tmp = GEN_LIB + ".%d.tmp" % os.getpid()
+    cmd = [cc, "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", GEN_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("host generator build failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    build_gen(force)
     if not force and not _stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)

@@ -25,21 +25,26 @@
 // Passes of one valuation (no host synchronisation between them):
 //   k_walk        nearest greater vertex by a direct walk of <= kWalkCap steps
 //   k_jump_coop   pointer jumping over smaller vertices for the rest
-//   k_chain1      g-subtree sizes and children counts (fire-and-forget atomics)
+//   k_chain1      classification, g-subtree sizes and children counts
 //   scan          children counts -> contiguous child segments
 //   k_scatter     children into their segments; the sink's children marked
-//   k_siblings    sibling weights inside each segment
-//   k_idscan_coop id-ordered scans for the sink (and parents with > kHugeChildren children)
-//   k_chain2      rank, depth and class by summing weights along each g-chain
-// The chain passes run a per-lane state machine: every loop step issues one
-// independent gather per lane, so a warp never waits on its longest chain.
+//   k_siblings    sibling weights inside each segment (k_big_parents for
+//                 large segments)
+//   sink scan     id-ordered scan for the children of each game's sink
+//   k_idscan_coop the same scan for parents with > kHugeChildren children
+//   k_chain2      rank and class by summing weights along each g-chain
+// The pointer-chasing passes give every thread several independent chains so
+// that several gathers are in flight per thread.
 //
-// Switching (Section 3, "Switching rules"; Section 4, All_Odd): a warp takes
-// 32 consecutive vertices, loads their edge lists in coalesced 32-edge chunks,
-// gathers the successors' ranks and reduces each list with a segmented
-// shuffle scan (first minimiser for Odd, first maximiser with the sink first
-// for Even); a vertex switches only when strictly better.
+// Switching (Section 3, "Switching rules"; Section 4, All_Odd): one thread
+// per vertex of the switching player, edges in batches of four gathers, first
+// minimiser for Odd, the sink first and then the first maximiser for Even; a
+// vertex switches only when strictly better.
+#include <cooperative_groups.h>
+
 #include "pg_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pg {
 namespace {
@@ -961,7 +966,12 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
         if (player == 0 ? bk > curkey : bk < curkey) {
             strat[v] = best;
             ++nsw;
-            if (vgame) atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, 1);
+            if (vgame) {  // one count per group of lanes of the same game
+                cg::coalesced_group sw = cg::coalesced_threads();
+                cg::coalesced_group same = cg::labeled_partition(sw, gi);
+                if (same.thread_rank() == 0)
+                    atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+            }
         }
     }
     block_add(nsw, &cnt->n_switch);

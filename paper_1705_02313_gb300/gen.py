@@ -19,7 +19,9 @@ ladder games, long successor chains, and batches of games of log-uniform size).
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -220,3 +222,89 @@ def named_config(name, seed=0):
     if name == "ladder-10m":         # n = 10,000,000 ladder
         return ladder_game(10_000_000, seed)
     raise KeyError(name)
+
+
+# ---------------------------------------------------------------------------
+# native generator (csrc/gen_host.c): the same random games, generated by C
+# worker threads straight into caller buffers
+
+_GEN = None
+
+
+def _gen_lib():
+    global _GEN
+    if _GEN is None:
+        from . import build
+        path = build.build_gen()
+        lib = ctypes.CDLL(path)
+        i64, u64p, i64p, vp = ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p, ctypes.c_void_p
+        lib.pggen_edge_counts.argtypes = [i64, i64p, u64p, i64, i64, i64p, ctypes.c_int]
+        lib.pggen_fill_batch.argtypes = [i64, i64p, u64p, i64, i64, ctypes.c_uint64, i64p, i64p, vp, vp, vp, vp,
+                                         ctypes.c_int]
+        lib.pggen_fill_game.argtypes = [i64, i64, i64, ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp,
+                                        ctypes.c_int]
+        _GEN = lib
+    return _GEN
+
+
+def _owner_threshold(p_odd):
+    return min(int(p_odd * 2.0**64), 2**64 - 1)
+
+
+def _threads(nthreads):
+    return int(nthreads or os.cpu_count() or 1)
+
+
+def _addr(x):
+    return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+
+
+def native_random_game(n, dmin, dmax, seed=0, p_odd=0.5, nthreads=0):
+    """random_game(n, dmin, dmax, seed, p_odd), generated by the C generator."""
+    lib = _gen_lib()
+    sizes = np.array([n], np.int64)
+    seeds = np.array([seed], np.uint64)
+    m = np.zeros(1, np.int64)
+    if lib.pggen_edge_counts(1, sizes.ctypes.data, seeds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), dmin, dmax,
+                             m.ctypes.data, 1):
+        raise ValueError("bad generator arguments")
+    if m[0] >= 2**31:
+        raise ValueError("edge count exceeds int32 CSR")
+    off = np.empty(n + 1, np.int32)
+    tgt = np.empty(int(m[0]), np.int32)
+    own = np.empty(n, np.uint8)
+    pri = np.empty(n, np.int32)
+    if lib.pggen_fill_game(n, dmin, dmax, seed, _owner_threshold(p_odd), off.ctypes.data, tgt.ctypes.data,
+                           own.ctypes.data, pri.ctypes.data, _threads(nthreads)):
+        raise ValueError("generator failed")
+    return Game(n, off, tgt, own, pri)
+
+
+def native_batch(count, lo, hi, dmin, dmax, p_odd=0.5, seed=0, nthreads=0, alloc=None):
+    """The batch of batch_games(count, lo, hi, dmin, dmax, p_odd, seed), packed
+    in the pg_solve_batch layout. ``alloc(shape_len, numpy_dtype)`` may supply
+    the four data buffers (for example pinned host tensors); by default numpy
+    arrays are used. Returns (vtx_base, edge_base, offsets, targets, owner, pri)."""
+    lib = _gen_lib()
+    sizes = log_uniform_sizes(count, lo, hi, seed).astype(np.int64)
+    seeds = np.array([batch_seed(i) for i in range(count)], np.uint64)
+    seeds_p = seeds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    ecount = np.zeros(count, np.int64)
+    nt = _threads(nthreads)
+    if lib.pggen_edge_counts(count, sizes.ctypes.data, seeds_p, dmin, dmax, ecount.ctypes.data, nt):
+        raise ValueError("bad generator arguments")
+    vtx_base = np.zeros(count + 1, np.int64)
+    edge_base = np.zeros(count + 1, np.int64)
+    np.cumsum(sizes, out=vtx_base[1:])
+    np.cumsum(ecount, out=edge_base[1:])
+    nv, ne = int(vtx_base[-1]), int(edge_base[-1])
+    alloc = alloc or (lambda length, dt: np.empty(length, dt))
+    off = alloc(nv + count, np.int32)
+    tgt = alloc(ne, np.int32)
+    own = alloc(nv, np.uint8)
+    pri = alloc(nv, np.int32)
+    if lib.pggen_fill_batch(count, sizes.ctypes.data, seeds_p, dmin, dmax, _owner_threshold(p_odd),
+                            vtx_base.ctypes.data, edge_base.ctypes.data, _addr(off), _addr(tgt), _addr(own),
+                            _addr(pri), nt):
+        raise ValueError("generator failed")
+    return vtx_base, edge_base, off, tgt, own, pri

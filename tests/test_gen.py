@@ -60,3 +60,21 @@ def test_log_uniform_sizes():
     s = gen.log_uniform_sizes(4096, 1000, 1_000_000)
     assert s.min() >= 1000 and s.max() <= 1_000_000
     assert 100_000 < s.mean() < 200_000
+
+
+def test_native_generator_matches_numpy():
+    # the C generator must produce exactly the numpy generator's games
+    for n, dmin, dmax, seed, p in [(1, 1, 1, 0, 0.5), (2, 1, 4, 3, 0.5), (1000, 1, 4, 0, 0.5), (3000, 2, 8, 7, 0.3),
+                                   (20000, 2, 6, gen.batch_seed(5), 0.5), (50, 40, 60, 1, 0.9)]:
+        a = gen.random_game(n, dmin, dmax, seed, p_odd=p)
+        b = gen.native_random_game(n, dmin, dmax, seed, p_odd=p, nthreads=3)
+        for x, y in zip(a.arrays(), b.arrays()):
+            assert x.dtype == y.dtype and np.array_equal(x, y), (n, seed)
+
+
+def test_native_batch_matches_packed_numpy_batch():
+    from paper_1705_02313_gb300 import pg
+    want = pg.pack_games(gen.batch_games(37, 3, 30000, 2, 6))
+    got = gen.native_batch(37, 3, 30000, 2, 6, nthreads=4)
+    for x, y in zip(want, got):
+        assert np.array_equal(x, y)
