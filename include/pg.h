@@ -251,6 +251,20 @@ pg_status pg_set_timing(pg_ctx *ctx, int32_t enable);
 pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuation_ms, double *switch_ms,
                          int64_t *valuations);
 
+/* How the iteration loop of pg_solve / pg_best_response / pg_solve_batch runs.
+ * With graphs enabled (the default) the whole loop is one CUDA graph launch: a
+ * conditional WHILE node repeats one iteration (valuation, switching passes,
+ * per-game bookkeeping) until no game is active, with no host synchronisation
+ * between iterations; the graph is built on first use per game and kept with
+ * it. With graphs disabled, or when timing is enabled, or if the CUDA runtime
+ * refuses to build the graph, the host launches each iteration and
+ * synchronises once per iteration. Both give identical results. The paper has
+ * no counterpart (it concerns launching work on the device only). */
+pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
+/* graph: 1 if the last loop on game ran as a graph, else 0; iterations: the
+ * valuations it computed (each may be NULL). */
+pg_status pg_last_loop(const pg_game *game, int32_t *graph, int64_t *iterations);
+
 #ifdef __cplusplus
 }
 #endif

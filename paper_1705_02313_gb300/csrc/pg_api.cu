@@ -28,10 +28,12 @@ void free_game(pg_game* g) {
                     g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
-                    g->tiles, g->cnt,    g->scan_tmp, g->stage};
+                    g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->hcnt) cudaFreeHost(g->hcnt);
+    for (auto& x : g->loop_exec)
+        if (x) cudaGraphExecDestroy(x);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : g->kev)
@@ -245,14 +247,125 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
 
 
 
+// Loop condition of the device-side loop: continue while a game is active,
+// no device error was recorded and the hard cap is not reached.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t* gactive, const Counters* c, int64_t* iters,
+                            int64_t hard_cap) {
+    const int64_t it = *iters + 1;
+    *iters = it;
+    cudaGraphSetConditional(h, (gactive[0] > 0 && c->err == 0 && it < hard_cap) ? 1u : 0u);
+}
+
+// One iteration of Algorithm 1 for every game of g (enqueued on ctx->stream).
+pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
+    pg_status st = enqueue_valuation(g, false);
+    if (!st) st = enqueue_switch(g, 1);
+    if (!st && even) st = enqueue_switch(g, 0);
+    if (!st) st = enqueue_bookkeeping(g, cap, even);
+    return st;
+}
+
+// Builds the loop graph: a WHILE node whose body is one iteration followed
+// by k_loop_cond. Returns false (nothing recorded) when the runtime refuses
+// any step; the caller then runs the loop from the host.
+bool build_loop_graph(pg_game* g, int64_t cap, bool even) {
+    pg_ctx* ctx = g->ctx;
+    const int w = even ? 1 : 0;
+    if (g->loop_exec[w] && g->loop_cap[w] == cap) return true;
+    if (g->loop_exec[w]) {
+        cudaGraphExecDestroy(g->loop_exec[w]);
+        g->loop_exec[w] = nullptr;
+    }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = false;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    const int64_t l0 = ctx->launches;
+    int64_t k0[KID_COUNT];
+    for (int i = 0; i < KID_COUNT; ++i) k0[i] = g->klaunch[i];
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t user = ctx->stream;
+        ctx->stream = ctx->cap_stream;
+        const bool quiet = ctx->quiet;
+        ctx->quiet = true;
+        ok = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            bool enq = enqueue_iteration(g, cap, even) == PG_OK;
+            if (enq) {
+                k_loop_cond<<<1, 1, 0, ctx->cap_stream>>>(h, g->gactive, g->cnt, g->loop_iters, cap + 2);
+                enq = cudaGetLastError() == cudaSuccess;
+            }
+            cudaGraph_t out = nullptr;
+            ok = cudaStreamEndCapture(ctx->cap_stream, &out) == cudaSuccess && enq;
+        }
+        ctx->stream = user;
+        ctx->quiet = quiet;
+    }
+    // launches counted while capturing belong to the iterations the graph will run
+    g->loop_launch[w] = ctx->launches - l0 + 1;
+    ctx->launches = l0;
+    for (int i = 0; i < KID_COUNT; ++i) {
+        g->loop_klaunch[w][i] = g->klaunch[i] - k0[i];
+        g->klaunch[i] = k0[i];
+    }
+    if (ok) ok = cudaGraphInstantiate(&g->loop_exec[w], graph, 0) == cudaSuccess;
+    cudaGraphDestroy(graph);
+    if (!ok) {
+        g->loop_exec[w] = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    g->loop_cap[w] = cap;
+    return true;
+}
+
 // Algorithm 1 for every game of g at once: each iteration computes the
 // valuation of every game, switches Odd in active games, switches Even in
 // games whose inner loop has converged (no Odd switch this iteration), and
 // updates each game's state on the device (see k_bookkeep). With even = false
-// only the inner loop runs (best responses). One host synchronisation per
-// iteration: the number of games still active.
+// only the inner loop runs (best responses). Normally the whole loop is one
+// CUDA graph launch whose WHILE node repeats the iteration until no game is
+// active (no host synchronisation between iterations); with timing enabled,
+// or where the runtime refuses the graph, the host runs the loop and
+// synchronises once per iteration.
 pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
     pg_ctx* ctx = g->ctx;
+    g->last_graph = false;
+    if (!tm.on && ctx->graphs && build_loop_graph(g, cap, even)) {
+        const int w = even ? 1 : 0;
+        cudaStream_t s = ctx->stream;
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(g->loop_iters, 0, sizeof(int64_t), s));
+        PG_CUDA_TRY(ctx, cudaGraphLaunch(g->loop_exec[w], s));
+        int64_t* it = (int64_t*)ctx->pinned;
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(it, g->loop_iters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        pg_status st = sync_counters(g);
+        const int64_t iters = *it;
+        g->t_vals += iters;
+        ctx->launches += g->loop_launch[w] * iters;
+        for (int i = 0; i < KID_COUNT; ++i) g->klaunch[i] += g->loop_klaunch[w][i] * iters;
+        g->last_graph = true;
+        if (st) return st;
+        if (iters > cap + 1) return fail(ctx, PG_ECUDA, "device-side loop exceeded its iteration cap");
+        return PG_OK;
+    }
     for (;;) {
         tm.mark(0);
         pg_status st = enqueue_valuation(g, false);
@@ -298,6 +411,7 @@ pg_status pg_ctx_create(pg_ctx** out, int device) {
 void pg_ctx_destroy(pg_ctx* ctx) {
     if (!ctx) return;
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -308,6 +422,19 @@ pg_status pg_set_stream(pg_ctx* ctx, void* stream) {
 }
 
 const char* pg_last_error(const pg_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
+    if (!ctx) return PG_EINVAL;
+    ctx->graphs = enable != 0;
+    return PG_OK;
+}
+
+pg_status pg_last_loop(const pg_game* g, int32_t* graph, int64_t* iterations) {
+    if (!g) return PG_EINVAL;
+    if (graph) *graph = g->last_graph ? 1 : 0;
+    if (iterations) *iterations = g->t_vals;
+    return PG_OK;
+}
 
 pg_status pg_set_timing(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;

@@ -115,6 +115,8 @@ struct pg_ctx {
     int32_t* pinned = nullptr;  // small pinned host buffer for counters
     int64_t launches = 0;       // kernels launched through this context
     bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
+    bool graphs = true;         // run the iteration loop as one CUDA graph with a device-side condition
+    cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
 
 // Per-game state of Algorithm 1 on the device (one entry per game of a batch).
@@ -188,6 +190,13 @@ struct pg_game {
     size_t scan_tmp_bytes = 0;
     int coop_blocks = 0;         // co-resident blocks for the cooperative kernels
     void* stage = nullptr;       // staging for host outputs
+    int64_t* loop_iters = nullptr;  // [1] iterations run by the device-side loop
+    // instantiated loop graphs: [0] inner loop only, [1] both players; built for loop_cap[i]
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    int64_t loop_cap[2] = {0, 0};
+    int64_t loop_launch[2] = {0, 0};                  // kernels per iteration of each graph
+    int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
+    bool last_graph = false;     // the last loop ran as a graph
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;

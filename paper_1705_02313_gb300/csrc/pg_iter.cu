@@ -1068,6 +1068,7 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A((void**)&g->gscan, sizeof(int64_t) * 3 * (size_t)g->ngames));
     PG_CUDA_TRY(ctx, A((void**)&g->gst, sizeof(GameState) * (size_t)g->ngames));
     PG_CUDA_TRY(ctx, A((void**)&g->gactive, sizeof(int32_t)));
+    PG_CUDA_TRY(ctx, A((void**)&g->loop_iters, sizeof(int64_t)));
     PG_CUDA_TRY(ctx, A((void**)&g->cnt, sizeof(Counters)));
     PG_CUDA_TRY(ctx, cudaMallocHost((void**)&g->hcnt, sizeof(Counters)));
     g->scan_tmp_bytes = scan_tmp_bytes(n + 2) + 64;

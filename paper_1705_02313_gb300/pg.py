@@ -92,6 +92,8 @@ def lib():
     L.pg_best_response.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
     L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
     L.pg_set_timing.argtypes = [P, I32]
+    L.pg_set_graphs.argtypes = [P, I32]
+    L.pg_last_loop.argtypes = [P, C.POINTER(I32), C.POINTER(I64)]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(I64)]
     L.pg_valuate_static.argtypes = [I32, P, P, P, P, P, P]
@@ -100,7 +102,7 @@ def lib():
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing"]:
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop"]:
         getattr(L, name).restype = I32
     _lib = L
     return L
@@ -319,6 +321,19 @@ def pg_valuate_static(n, succ, odd, val_class=None, val_depth=None, val_rank=Non
 
 def pg_set_timing(ctx, enable):
     _check(ctx, lib().pg_set_timing(ctx, 1 if enable else 0), "pg_set_timing")
+
+
+def pg_set_graphs(ctx, enable):
+    _check(ctx, lib().pg_set_graphs(ctx, 1 if enable else 0), "pg_set_graphs")
+
+
+def pg_last_loop(game):
+    """(ran_as_graph, iterations) of the last loop on game."""
+    gr, it = C.c_int32(), C.c_int64()
+    rc = lib().pg_last_loop(game, C.byref(gr), C.byref(it))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_last_loop")
+    return bool(gr.value), it.value
 
 
 def pg_last_timing(game):
