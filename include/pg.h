@@ -211,6 +211,71 @@ pg_status pg_solve_batch(pg_ctx *ctx, int32_t ngames, const int64_t *vtx_base, c
                          const int32_t *offsets, const int32_t *targets, const uint8_t *owner, const int32_t *pri,
                          int32_t mem_kind, int64_t max_inner, pg_result_batch *out);
 
+/* ---- Serving: continuous batching of a stream of games ----------------------
+ *
+ * A server owns one CUDA stream on one device, a worker thread and a packed
+ * batch allocated once at its capacity. pg_server_submit copies a game into a
+ * FIFO queue and returns at once. Between rounds the worker retires finished
+ * games and admits queued ones in arrival order while they fit the capacity
+ * (vertices after preprocessing plus one sink slot each, edges, games); a
+ * round runs Algorithm 1 (Section 4) over all resident games for at most
+ * round_iters iterations. Each game keeps its strategies and loop state on
+ * the device across rounds, so its result is exactly the one pg_solve gives
+ * for it alone, whatever else is resident. The paper has no counterpart (it
+ * solves one game at a time). */
+typedef struct pg_server pg_server;
+
+typedef struct {
+    int64_t max_vertices;  /* capacity in ids (G' vertices + 1 per game); 0 = from free device memory */
+    int64_t max_edges;     /* capacity in G' edges; 0 = from free device memory */
+    int32_t max_games;     /* resident games; 0 = 4096 */
+    int32_t round_iters;   /* iterations per round (admission points); 0 = 8 */
+    int64_t max_inner;     /* per-game iteration cap; 0 = 64 (largest resident n' + 64) */
+} pg_server_opts;
+
+/* One finished game, as reported by pg_server_poll. */
+typedef struct {
+    uint64_t tag;       /* the caller's tag from pg_server_submit */
+    int32_t status;     /* PG_OK, PG_ETIMEOUT, PG_ENOTADMISSIBLE, or the load error (PG_EINVAL, PG_EUNSUPPORTED,
+                           PG_ENOMEM when the game alone exceeds the capacity) */
+    int32_t n;          /* original vertices */
+    int32_t k;          /* dummies */
+    int64_t major, inner;
+    double queue_us;    /* submission to admission */
+    double latency_us;  /* submission to result */
+} pg_served;
+
+typedef struct {
+    int64_t submitted, admitted, completed, queued;
+    int64_t admitted_while_busy;  /* games admitted while other games were resident */
+    int64_t rounds, iterations, max_resident;
+    int64_t capacity_vertices, capacity_edges;
+} pg_server_stats;
+
+/* Creates a server on device; opts may be NULL (defaults). */
+pg_status pg_server_create(int device, const pg_server_opts *opts, pg_server **out);
+/* Stops the worker (games in flight are abandoned) and frees everything. */
+void pg_server_destroy(pg_server *server);
+/* Queues a game given by host arrays (layout as pg_load_csr); the arrays are
+ * copied before the call returns. tag must not be in use by a queued,
+ * resident or unfetched game (PG_EINVAL). Validation happens at admission:
+ * an invalid game finishes with the load error as its status. */
+pg_status pg_server_submit(pg_server *server, int32_t n, int64_t m, const int32_t *offsets, const int32_t *targets,
+                           const uint8_t *owner, const int32_t *pri, uint64_t tag);
+/* Reports up to max finished games in completion order, waiting up to
+ * timeout_ms for the first one; *count receives the number written. Returns
+ * the server's error (PG_ECUDA ...) if its worker failed and nothing is left
+ * to report. */
+pg_status pg_server_poll(pg_server *server, pg_served *out, int32_t max, int32_t timeout_ms, int32_t *count);
+/* Copies a reported game's results into caller host arrays (each may be
+ * NULL; layouts as in pg_result, n entries, dummy_sigma k entries) and
+ * releases them. PG_EINVAL for an unknown or not yet reported tag. */
+pg_status pg_server_fetch(pg_server *server, uint64_t tag, uint8_t *win, int32_t *sigma, int32_t *tau,
+                          int8_t *val_class, int32_t *val_depth, int32_t *val_rank, int8_t *dummy_sigma);
+pg_status pg_server_get_stats(pg_server *server, pg_server_stats *out);
+/* The message of the worker's failure, or "no error". */
+const char *pg_server_error(pg_server *server);
+
 /* Valuation of one successor function without allocating any memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory themselves or let a library do it, for example code

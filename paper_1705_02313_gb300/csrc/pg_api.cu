@@ -22,6 +22,14 @@ pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where) {
     return code;
 }
 
+void drop_loop_graphs(pg_game* g) {
+    for (int i = 0; i < 2; ++i) {
+        if (g->loop_exec[i]) cudaGraphExecDestroy(g->loop_exec[i]);
+        g->loop_exec[i] = nullptr;
+        g->loop_cap[i] = g->loop_limit[i] = 0;
+    }
+}
+
 void free_game(pg_game* g) {
     if (!g) return;
     void* ptrs[] = {g->off,  g->off64,   g->vgame, g->gsink, g->gst,   g->gactive, g->gscan,
@@ -159,7 +167,7 @@ Stage stage_layout(int64_t n0, int64_t k) {
 }  // namespace
 
 pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
-                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig) {
+                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig, bool depth_ready) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     OutPtrs o = {win, sigma, tau, vclass, vdepth, vrank, vdom, dsig};
@@ -172,7 +180,7 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
              vdepth ? (int32_t*)(b + L.off_depth) : nullptr, vrank ? (int32_t*)(b + L.off_rank) : nullptr,
              vdom ? (int32_t*)(b + L.off_dom) : nullptr,     dsig ? (int8_t*)(b + L.off_dsig) : nullptr};
     }
-    if (vdepth) {
+    if (vdepth && !depth_ready) {
         pg_status st = enqueue_depth(g);
         if (st) return st;
     }
@@ -268,10 +276,10 @@ pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
 // Builds the loop graph: a WHILE node whose body is one iteration followed
 // by k_loop_cond. Returns false (nothing recorded) when the runtime refuses
 // any step; the caller then runs the loop from the host.
-bool build_loop_graph(pg_game* g, int64_t cap, bool even) {
+bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     const int w = even ? 1 : 0;
-    if (g->loop_exec[w] && g->loop_cap[w] == cap) return true;
+    if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit) return true;
     if (g->loop_exec[w]) {
         cudaGraphExecDestroy(g->loop_exec[w]);
         g->loop_exec[w] = nullptr;
@@ -310,7 +318,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even) {
         if (ok) {
             bool enq = enqueue_iteration(g, cap, even) == PG_OK;
             if (enq) {
-                k_loop_cond<<<1, 1, 0, ctx->cap_stream>>>(h, g->gactive, g->cnt, g->loop_iters, cap + 2);
+                k_loop_cond<<<1, 1, 0, ctx->cap_stream>>>(h, g->gactive, g->cnt, g->loop_iters, limit);
                 enq = cudaGetLastError() == cudaSuccess;
             }
             cudaGraph_t out = nullptr;
@@ -334,6 +342,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even) {
         return false;
     }
     g->loop_cap[w] = cap;
+    g->loop_limit[w] = limit;
     return true;
 }
 
@@ -345,11 +354,14 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even) {
 // CUDA graph launch whose WHILE node repeats the iteration until no game is
 // active (no host synchronisation between iterations); with timing enabled,
 // or where the runtime refuses the graph, the host runs the loop and
-// synchronises once per iteration.
-pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
+// synchronises once per iteration. A positive limit ends the call after that
+// many iterations even if games are still active (their state stays on the
+// device and a later call continues them).
+pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     g->last_graph = false;
-    if (!tm.on && ctx->graphs && build_loop_graph(g, cap, even)) {
+    const int64_t hard = limit > 0 ? std::min<int64_t>(limit, cap + 2) : cap + 2;
+    if (!tm.on && ctx->graphs && build_loop_graph(g, cap, even, hard)) {
         const int w = even ? 1 : 0;
         cudaStream_t s = ctx->stream;
         PG_CUDA_TRY(ctx, cudaMemsetAsync(g->loop_iters, 0, sizeof(int64_t), s));
@@ -363,10 +375,10 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
         for (int i = 0; i < KID_COUNT; ++i) g->klaunch[i] += g->loop_klaunch[w][i] * iters;
         g->last_graph = true;
         if (st) return st;
-        if (iters > cap + 1) return fail(ctx, PG_ECUDA, "device-side loop exceeded its iteration cap");
+        if (iters > hard) return fail(ctx, PG_ECUDA, "device-side loop exceeded its iteration cap");
         return PG_OK;
     }
-    for (;;) {
+    for (int64_t it = 1;; ++it) {
         tm.mark(0);
         pg_status st = enqueue_valuation(g, false);
         if (st) return st;
@@ -382,7 +394,7 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm) {
         ++g->t_vals;
         g->t_val += tm.since(0, 1);
         g->t_switch += tm.since(1, 2);
-        if (ctx->pinned[0] == 0) return PG_OK;
+        if (ctx->pinned[0] == 0 || it >= hard) return PG_OK;
     }
 }
 

@@ -194,6 +194,7 @@ struct pg_game {
     // instantiated loop graphs: [0] inner loop only, [1] both players; built for loop_cap[i]
     cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
     int64_t loop_cap[2] = {0, 0};
+    int64_t loop_limit[2] = {0, 0};
     int64_t loop_launch[2] = {0, 0};                  // kernels per iteration of each graph
     int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
     bool last_graph = false;     // the last loop ran as a graph
@@ -240,10 +241,14 @@ struct Timer {
 // Sets g->strat from a profile in original ids (NULL arrays: the initial profile).
 pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, const int8_t* dsig, int32_t mem_kind);
 // Writes results in original ids (host or device arrays; NULL skips).
+// depth_ready: the depth pass already ran after the last valuation.
 pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
-                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig);
+                        int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig, bool depth_ready = false);
 // Algorithm 1 for all games of g (even = false: inner loop only).
-pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm);
+// limit > 0: return after at most limit iterations (games may still be active).
+pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit = 0);
+// Launches of the iteration loop graph are invalidated (sizes of g changed).
+void drop_loop_graphs(pg_game* g);
 // Packs loaded single games (freed by the call) into one batch game.
 pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out);
 // Per-game loop bookkeeping after the switching passes; counts active games.

@@ -57,6 +57,22 @@ class pg_result_batch(C.Structure):
                 ("dummy_base", C.c_void_p), ("iterations", C.c_int64)]
 
 
+class pg_server_opts(C.Structure):
+    _fields_ = [("max_vertices", C.c_int64), ("max_edges", C.c_int64), ("max_games", C.c_int32),
+                ("round_iters", C.c_int32), ("max_inner", C.c_int64)]
+
+
+class pg_served(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("n", C.c_int32), ("k", C.c_int32),
+                ("major", C.c_int64), ("inner", C.c_int64), ("queue_us", C.c_double), ("latency_us", C.c_double)]
+
+
+class pg_server_stats(C.Structure):
+    _fields_ = [(nm, C.c_int64) for nm in ["submitted", "admitted", "completed", "queued", "admitted_while_busy",
+                                           "rounds", "iterations", "max_resident", "capacity_vertices",
+                                           "capacity_edges"]]
+
+
 class pg_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_double), ("launches", C.c_int64), ("calls", C.c_int64)]
 
@@ -98,11 +114,21 @@ def lib():
                                  C.POINTER(I64)]
     L.pg_valuate_static.argtypes = [I32, P, P, P, P, P, P]
     L.pg_solve_batch.argtypes = [P, I32, P, P, P, P, P, P, I32, I64, C.POINTER(pg_result_batch)]
+    L.pg_server_create.argtypes = [C.c_int, C.POINTER(pg_server_opts), C.POINTER(P)]
+    L.pg_server_destroy.argtypes = [P]
+    L.pg_server_destroy.restype = None
+    L.pg_server_submit.argtypes = [P, I32, I64, P, P, P, P, C.c_uint64]
+    L.pg_server_poll.argtypes = [P, C.POINTER(pg_served), I32, I32, C.POINTER(I32)]
+    L.pg_server_fetch.argtypes = [P, C.c_uint64, P, P, P, P, P, P, P]
+    L.pg_server_get_stats.argtypes = [P, C.POINTER(pg_server_stats)]
+    L.pg_server_error.argtypes = [P]
+    L.pg_server_error.restype = C.c_char_p
     L.pg_kernel_stats.argtypes = [P, C.POINTER(pg_kernel_stat), I32, C.POINTER(I32)]
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop"]:
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop", "pg_server_create", "pg_server_submit", "pg_server_poll",
+                 "pg_server_fetch", "pg_server_get_stats"]:
         getattr(L, name).restype = I32
     _lib = L
     return L
@@ -297,6 +323,64 @@ def pack_games(games):
     owner = np.concatenate([g.owner for g in games]).astype(np.uint8)
     pri = np.concatenate([g.pri for g in games]).astype(np.int32)
     return vtx_base, edge_base, offsets, targets, owner, pri
+
+
+def pg_server_create(device=0, max_vertices=0, max_edges=0, max_games=0, round_iters=0, max_inner=0):
+    opts = pg_server_opts(int(max_vertices), int(max_edges), int(max_games), int(round_iters), int(max_inner))
+    sv = C.c_void_p()
+    rc = lib().pg_server_create(int(device), C.byref(opts), C.byref(sv))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_server_create")
+    return sv
+
+
+def pg_server_destroy(server):
+    lib().pg_server_destroy(server)
+
+
+def pg_server_submit(server, n, m, offsets, targets, owner, pri, tag):
+    """Queues a game (host arrays, copied before the call returns)."""
+    arrs = [np.ascontiguousarray(offsets, np.int32), np.ascontiguousarray(targets, np.int32),
+            np.ascontiguousarray(owner, np.uint8), np.ascontiguousarray(pri, np.int32)]
+    rc = lib().pg_server_submit(server, int(n), int(m), *[a.ctypes.data for a in arrs], int(tag))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_server_submit")
+
+
+def pg_server_poll(server, max_results=64, timeout_ms=0):
+    """Finished games in completion order: a list of dicts."""
+    buf = (pg_served * max(1, int(max_results)))()
+    cnt = C.c_int32(0)
+    rc = lib().pg_server_poll(server, buf, int(max_results), int(timeout_ms), C.byref(cnt))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_server_poll: " + pg_server_error(server))
+    return [{f: getattr(buf[i], f) for f, _ in pg_served._fields_} for i in range(cnt.value)]
+
+
+def pg_server_fetch(server, tag, n, k):
+    """Results of a reported game as numpy arrays (and releases them)."""
+    out = dict(win=np.empty(n, np.uint8), sigma=np.empty(n, np.int32), tau=np.empty(n, np.int32),
+               val_class=np.empty(n, np.int8), val_depth=np.empty(n, np.int32), val_rank=np.empty(n, np.int32),
+               dummy_sigma=np.empty(max(k, 1), np.int8))
+    rc = lib().pg_server_fetch(server, int(tag), *[out[x].ctypes.data for x in
+                                                   ["win", "sigma", "tau", "val_class", "val_depth", "val_rank",
+                                                    "dummy_sigma"]])
+    if rc != PG_OK:
+        raise PgError(rc, "pg_server_fetch")
+    out["dummy_sigma"] = out["dummy_sigma"][:k]
+    return out
+
+
+def pg_server_get_stats(server):
+    st = pg_server_stats()
+    rc = lib().pg_server_get_stats(server, C.byref(st))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_server_get_stats")
+    return {f: getattr(st, f) for f, _ in pg_server_stats._fields_}
+
+
+def pg_server_error(server):
+    return lib().pg_server_error(server).decode()
 
 
 def pg_valuate_static(n, succ, odd, val_class=None, val_depth=None, val_rank=None, stream=None):
