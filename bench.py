@@ -246,6 +246,94 @@ def batch_measure(name):
 
 
 # ---------------------------------------------------------------------------
+# serving: a Poisson stream of games through pg_server_*
+
+SERVE = {
+    "serve-200": dict(rate=200.0, lo=10_000, hi=4_000_000, dmin=2, dmax=6, pool=64,
+                      desc="Poisson arrivals at 200 games/s; random games with sizes log-uniform in [1e4, 4e6], "
+                           "out-degree U[2,6], owners p=0.5, permuted priorities; arrival j is game j mod 64 of a "
+                           "pool generated with seeds SplitMix64(0x5EED ^ i)"),
+}
+
+
+def serve_measure(name, seconds):
+    """Submits arrivals of a Poisson process for ``seconds`` from one thread,
+    polls results from another, then solves the pool one game at a time
+    (pg_load_csr + pg_solve from host arrays) for comparison."""
+    import threading
+
+    import torch
+
+    from paper_1705_02313_gb300 import gen, pg
+    cfg = SERVE[name]
+    t0 = time.perf_counter()
+    vb, eb, off, tgt, own, pri = gen.native_batch(cfg["pool"], cfg["lo"], cfg["hi"], cfg["dmin"], cfg["dmax"])
+    t_gen = time.perf_counter() - t0
+    P = cfg["pool"]
+    pool = [(int(vb[i + 1] - vb[i]), int(eb[i + 1] - eb[i]), off[int(vb[i]) + i:int(vb[i + 1]) + i + 1],
+             tgt[int(eb[i]):int(eb[i + 1])], own[int(vb[i]):int(vb[i + 1])], pri[int(vb[i]):int(vb[i + 1])])
+            for i in range(P)]
+    rng = np.random.default_rng(12345)
+    gaps = rng.exponential(1.0 / cfg["rate"], size=int(cfg["rate"] * seconds * 2) + 16)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < seconds]
+    sv = pg.pg_server_create(0)
+    done = {}
+    submit_err = []
+
+    def submitter():
+        start = time.perf_counter()
+        try:
+            for j, ta in enumerate(arrivals):
+                d = ta - (time.perf_counter() - start)
+                if d > 0:
+                    time.sleep(d)
+                n, m, o, t, w, p = pool[j % P]
+                pg.pg_server_submit(sv, n, m, o, t, w, p, tag=j)
+        except Exception as e:  # reported in the result
+            submit_err.append(repr(e))
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    limit = seconds + 120.0
+    while len(done) < len(arrivals) and time.perf_counter() - t_start < limit:
+        for r in pg.pg_server_poll(sv, 256, 50):
+            done[r["tag"]] = (r, time.perf_counter())
+            pg.pg_server_fetch(sv, r["tag"], r["n"], r["k"], keep=False)
+    th.join()
+    t_last = max((x[1] for x in done.values()), default=time.perf_counter())
+    stats = pg.pg_server_get_stats(sv)
+    pg.pg_server_destroy(sv)
+    lat = np.array([x[0]["latency_us"] for x in done.values()]) / 1e3
+    qus = np.array([x[0]["queue_us"] for x in done.values()]) / 1e3
+    ok = sum(1 for x in done.values() if x[0]["status"] == pg.PG_OK)
+    served = len(done) / (t_last - t_start) if done else 0.0
+    # one at a time over the pool (host arrays, as submitted)
+    ctx = pg.pg_ctx_create(0)
+    t0 = time.perf_counter()
+    for (n, m, o, t, w, p) in pool:
+        g = pg.pg_load_csr(ctx, n, m, o, t, w, p)
+        try:
+            pg.pg_solve(ctx, g, win=np.empty(n, np.uint8))
+        finally:
+            pg.pg_game_free(g)
+    t_single = time.perf_counter() - t0
+    pg.pg_ctx_destroy(ctx)
+    torch.cuda.synchronize()
+    return {"workload": name, "description": cfg["desc"], "seconds": seconds, "arrivals": int(len(arrivals)),
+            "completed": len(done), "ok": ok, "metric": "served games/s and latency", "unit": "games/s",
+            "served_games_per_s": served, "offered_games_per_s": len(arrivals) / seconds,
+            "latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
+            "latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
+            "queue_ms_p50": float(np.percentile(qus, 50)) if qus.size else None,
+            "one_at_a_time_games_per_s": P / t_single, "pool_games": P,
+            "pool_vertices": int(vb[-1]), "pool_edges": int(eb[-1]), "generate_s": t_gen,
+            "server": stats, "submit_errors": submit_err,
+            "timing": "wall clock; latency from submission to result, measured by the server"}
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample
 
 def cpu_sample(game, iters):
@@ -440,6 +528,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_measure(args.batch)
+    if rank == 0 and args.serve > 0:
+        line["serve"] = serve_measure("serve-200", args.serve)
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_sample(game, args.cpu_iters)
         line["cpu_baseline"] = {"value": r["edges"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -496,6 +586,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-one-at-a-time measurement")
+    ap.add_argument("--serve", type=float, default=10.0,
+                    help="seconds of the Poisson serving stream measured beside the main line (0: skip)")
     ap.add_argument("--batch", choices=sorted(BATCHES), default="batch-256",
                     help="batch workload measured beside the main line")
     args = ap.parse_args()

@@ -178,14 +178,19 @@ cudaError_t dalloc(T** p, int64_t count) {
     return cudaMalloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T));
 }
 
+// Temporaries of one load, stream-ordered on the load's stream (allocating
+// and freeing them does not synchronise the device, so loads can overlap
+// other streams' work).
 struct Temps {
+    cudaStream_t s;
     std::vector<void*> ptrs;
+    explicit Temps(cudaStream_t st) : s(st) {}
     ~Temps() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) cudaFreeAsync(p, s);
     }
     template <typename T>
     cudaError_t get(T** p, int64_t count) {
-        cudaError_t e = dalloc(p, count);
+        cudaError_t e = cudaMallocAsync((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
         if (e == cudaSuccess) ptrs.push_back((void*)*p);
         return e;
     }
@@ -203,7 +208,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     if (m < n || m > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: m must be in [n, 2^31-1)");
     cudaStream_t s = ctx->stream;
     cudaMemcpyKind kind = mem_kind == PG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    Temps T;
+    Temps T(s);
     int32_t *off, *tgt, *pri;
     uint8_t* own;
     LoadScalars* sc;

@@ -1,14 +1,16 @@
 // Serving: a request loop with continuous batching (pg_server_*).
 //
-// A worker thread owns a CUDA stream and a packed batch allocated once at the
-// server's capacity (ids, edges, games). Submitted games wait in a FIFO queue
-// (host copies of their arrays). Between rounds the worker retires finished
-// games and admits queued ones while they fit the capacity; every game keeps
-// its strategy profile and its loop state (Algorithm 1, Section 4: inner and
-// major counts, phase) across rounds, so its trajectory, and therefore its
-// result, is exactly the one pg_solve gives for it alone. A round is the
-// device-side loop over all resident games for at most round_iters
-// iterations; games that arrive meanwhile join at the next round.
+// Two threads, each with its own CUDA stream. The loader takes submitted
+// games (host copies of their arrays) from a FIFO queue and loads them
+// (validation, the preprocessing of Section 3, relabelling, the initial
+// profile) while the worker is solving: their work overlaps on the device.
+// The worker owns a packed batch allocated once at the server's capacity
+// (ids, edges, games). Between rounds it retires finished games and admits
+// loaded ones in arrival order while they fit; every game keeps its strategy
+// profile and its loop state (Algorithm 1, Section 4: inner and major counts,
+// phase) across rounds, so its trajectory, and therefore its result, is
+// exactly the one pg_solve gives for it alone. A round is the device-side
+// loop over all resident games for at most round_iters iterations.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -115,12 +117,16 @@ struct Done {
 using namespace pg;
 
 struct pg_server {
-    pg_ctx* ctx = nullptr;
+    pg_ctx* ctx = nullptr;   // the worker's
+    pg_ctx* lctx = nullptr;  // the loader's
     pg_server_opts opts{};
-    std::thread worker;
+    std::thread worker, loader;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Pending> queue;
+    std::condition_variable cv_work, cv_done, cv_load;
+    std::deque<Pending> queue;       // submitted, not loaded
+    std::deque<Resident> ready;      // loaded, not admitted
+    int64_t ready_ids = 0;
+    std::map<uint64_t, int> inflight;  // tags of resident games (for duplicate checks)
     std::map<uint64_t, Done> done;
     std::deque<uint64_t> done_order;  // completion order, not yet reported by pg_server_poll
     bool stop = false;
@@ -129,8 +135,8 @@ struct pg_server {
     pg_server_stats stats{};
     // worker-only state
     std::vector<Resident> res;
+    size_t packed_count = 0;  // res[0 .. packed_count) are laid out in the packed batch
     pg_game* B = nullptr;  // packed batch at capacity
-    bool packed = false;
     int64_t capN = 0, capM = 0;
     int32_t capG = 0;
 };
@@ -162,13 +168,15 @@ pg_status alloc_batch(pg_server* sv) {
     return alloc_scratch(g);
 }
 
-void set_fatal(pg_server* sv, pg_status st) {
+void set_fatal(pg_server* sv, pg_status st, pg_ctx* from) {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->fatal == PG_OK) {
         sv->fatal = st;
-        sv->fatal_msg = sv->ctx->err;
+        sv->fatal_msg = from->err;
     }
     sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+    sv->cv_load.notify_all();
 }
 
 void finish_pending_error(pg_server* sv, const Pending& p, pg_status st) {
@@ -178,6 +186,7 @@ void finish_pending_error(pg_server* sv, const Pending& p, pg_status st) {
     d.t_submit = p.t_submit;
     d.t_admit = d.t_done = now_us();
     std::lock_guard<std::mutex> lk(sv->mu);
+    sv->inflight.erase(p.tag);
     sv->done[p.tag] = std::move(d);
     sv->done_order.push_back(p.tag);
     sv->stats.completed += 1;
@@ -240,17 +249,17 @@ pg_status repack(pg_server* sv) {
     // reset_scratch clears the loop states: put them back
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(g->gst, hst.data(), sizeof(GameState) * hst.size(), cudaMemcpyHostToDevice, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    sv->packed = true;
     return PG_OK;
 }
 
-// Profiles of the games that stay resident back into their own arrays.
+// Profiles of the games that stay resident back into their own arrays
+// (keep covers the games of the current layout, a prefix of res).
 pg_status unpack_profiles(pg_server* sv, const std::vector<bool>& keep) {
     pg_ctx* ctx = sv->ctx;
     pg_game* g = sv->B;
     cudaStream_t s = ctx->stream;
     int64_t Bb = 0;
-    for (size_t i = 0; i < sv->res.size(); ++i) {
+    for (size_t i = 0; i < keep.size(); ++i) {
         pg_game* gi = sv->res[i].g;
         if (keep[i]) {
             ctx->launches += 1;
@@ -291,93 +300,127 @@ pg_status collect(pg_server* sv, size_t i, Done* d) {
     return st;
 }
 
+// Loads queued games on the loader's stream while the worker solves, up to
+// the capacity's worth of loaded games waiting for admission.
+void loader_main(pg_server* sv) {
+    pg_ctx* ctx = sv->lctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        set_fatal(sv, PG_ECUDA, ctx);
+        return;
+    }
+    for (;;) {
+        Pending p;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_load.wait(lk, [&] {
+                return sv->stop || sv->fatal ||
+                       (!sv->queue.empty() && sv->ready_ids < sv->capN && (int64_t)sv->ready.size() < sv->capG);
+            });
+            if (sv->stop || sv->fatal) return;
+            p = std::move(sv->queue.front());
+            sv->queue.pop_front();
+            sv->inflight[p.tag] = 1;
+        }
+        pg_game* gi = nullptr;
+        pg_status st = load_game(ctx, p.n, p.m, p.off.data(), p.tgt.data(), p.own.data(), p.pri.data(), PG_MEM_HOST,
+                                 &gi, false);
+        if (st != PG_OK) {
+            if (st == PG_ECUDA) {
+                set_fatal(sv, st, ctx);
+                return;
+            }
+            finish_pending_error(sv, p, st);
+            continue;
+        }
+        ctx->launches += 1;
+        k_init_profile<<<grid_of(gi->n), kBlock, 0, ctx->stream>>>(gi->n - 1, gi->off, gi->tgt, gi->flags, gi->strat);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            free_game(gi);
+            set_fatal(sv, PG_ECUDA, ctx);
+            return;
+        }
+        Resident r{};
+        r.tag = p.tag;
+        r.g = gi;
+        r.t_submit = p.t_submit;
+        r.slot = -1;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->ready_ids += gi->n;
+            sv->ready.push_back(r);
+        }
+        sv->cv_work.notify_all();
+    }
+}
+
 void worker_main(pg_server* sv) {
     pg_ctx* ctx = sv->ctx;
     if (cudaSetDevice(ctx->device) != cudaSuccess) {
-        set_fatal(sv, PG_ECUDA);
+        set_fatal(sv, PG_ECUDA, ctx);
         return;
     }
     const int64_t round_iters = sv->opts.round_iters > 0 ? sv->opts.round_iters : 8;
     bool changed = false;
     for (;;) {
-        // admission: queued games in arrival order while they fit
+        // admission: loaded games in arrival order while they fit
         for (;;) {
-            Pending p;
+            Resident r;
             {
                 std::unique_lock<std::mutex> lk(sv->mu);
-                if (sv->stop) return;
-                if (sv->queue.empty()) {
+                if (sv->stop || sv->fatal) return;
+                if (sv->ready.empty()) {
                     if (!sv->res.empty()) break;
-                    sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty(); });
-                    if (sv->stop) return;
+                    sv->cv_work.wait(lk, [&] { return sv->stop || sv->fatal || !sv->ready.empty(); });
+                    if (sv->stop || sv->fatal) return;
                 }
                 int64_t N = 0, M = 0;
-                for (const Resident& r : sv->res) {
-                    N += r.g->n;
-                    M += r.g->m;
+                for (const Resident& x : sv->res) {
+                    N += x.g->n;
+                    M += x.g->m;
                 }
-                const Pending& q = sv->queue.front();
-                // G' has at most 2n vertices (n + dummies) plus the sink slot and at most m + n edges; a game
-                // that might not fit waits until it is alone, then its actual size decides
-                const int64_t need_n = 2 * (int64_t)q.n + 1, need_m = q.m + q.n;
-                const bool fits = N + need_n <= sv->capN && M + need_m <= sv->capM &&
+                const Resident& q = sv->ready.front();
+                const bool fits = N + q.g->n <= sv->capN && M + q.g->m <= sv->capM &&
                                   (int64_t)sv->res.size() < sv->capG;
                 if (!fits && !sv->res.empty()) break;
-                p = std::move(sv->queue.front());
-                sv->queue.pop_front();
-            }
-            pg_game* gi = nullptr;
-            pg_status st = load_game(ctx, p.n, p.m, p.off.data(), p.tgt.data(), p.own.data(), p.pri.data(),
-                                     PG_MEM_HOST, &gi, false);
-            if (st != PG_OK) {
-                if (st == PG_ECUDA) {
-                    set_fatal(sv, st);
-                    return;
+                r = sv->ready.front();
+                sv->ready.pop_front();
+                sv->ready_ids -= r.g->n;
+                if (fits) {
+                    sv->stats.admitted += 1;
+                    if (!sv->res.empty()) sv->stats.admitted_while_busy += 1;
                 }
-                finish_pending_error(sv, p, st);
+            }
+            sv->cv_load.notify_all();
+            if (!(r.g->n <= sv->capN && r.g->m <= sv->capM)) {  // larger than the whole capacity
+                Pending p;
+                p.tag = r.tag;
+                p.n = (int32_t)r.g->n0;
+                p.t_submit = r.t_submit;
+                free_game(r.g);
+                finish_pending_error(sv, p, PG_ENOMEM);
                 continue;
             }
-            {
-                int64_t N = 0, M = 0;
-                for (const Resident& r : sv->res) {
-                    N += r.g->n;
-                    M += r.g->m;
-                }
-                if (N + gi->n > sv->capN || M + gi->m > sv->capM) {  // larger than the whole capacity
-                    free_game(gi);
-                    finish_pending_error(sv, p, PG_ENOMEM);
-                    continue;
-                }
-            }
-            ctx->launches += 1;
-            k_init_profile<<<grid_of(gi->n), kBlock, 0, ctx->stream>>>(gi->n - 1, gi->off, gi->tgt, gi->flags,
-                                                                      gi->strat);
-            if (cudaGetLastError() != cudaSuccess) {
-                free_game(gi);
-                set_fatal(sv, PG_ECUDA);
-                return;
-            }
-            Resident r{};
-            r.tag = p.tag;
-            r.g = gi;
-            r.t_submit = p.t_submit;
             r.t_admit = now_us();
-            r.slot = -1;
-            {
-                std::lock_guard<std::mutex> lk(sv->mu);
-                sv->stats.admitted += 1;
-                if (!sv->res.empty()) sv->stats.admitted_while_busy += 1;
-            }
             sv->res.push_back(r);
             changed = true;
         }
         if (sv->res.empty()) continue;
         pg_status st = PG_OK;
         if (changed) {
+            // profiles of the games already in the batch come out first: the new layout starts from them
+            if (sv->packed_count > 0) {
+                std::vector<bool> all(sv->packed_count, true);
+                st = unpack_profiles(sv, all);
+                if (st) {
+                    set_fatal(sv, st, ctx);
+                    return;
+                }
+            }
             st = repack(sv);
+            sv->packed_count = sv->res.size();
             changed = false;
             if (st) {
-                set_fatal(sv, st);
+                set_fatal(sv, st, ctx);
                 return;
             }
         }
@@ -392,12 +435,14 @@ void worker_main(pg_server* sv) {
         Timer tm(sv->B);
         st = run_loop(sv->B, cap, true, tm, round_iters);
         if (st) {
-            set_fatal(sv, st);
+            set_fatal(sv, st, ctx);
             return;
         }
         std::vector<GameState> gs(sv->res.size());
-        if (cudaMemcpy(gs.data(), sv->B->gst, sizeof(GameState) * gs.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            set_fatal(sv, PG_ECUDA);
+        if (cudaMemcpyAsync(gs.data(), sv->B->gst, sizeof(GameState) * gs.size(), cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            set_fatal(sv, PG_ECUDA, ctx);
             return;
         }
         bool any_done = false, any_timeout = false;
@@ -420,13 +465,13 @@ void worker_main(pg_server* sv) {
             st = enqueue_valuation(sv->B, false);
             if (!st) st = sync_counters(sv->B);
             if (st) {
-                set_fatal(sv, st);
+                set_fatal(sv, st, ctx);
                 return;
             }
         }
         st = enqueue_depth(sv->B);  // once for every finished game of this round
         if (st) {
-            set_fatal(sv, st);
+            set_fatal(sv, st, ctx);
             return;
         }
         std::vector<std::pair<uint64_t, Done>> fin;
@@ -435,7 +480,7 @@ void worker_main(pg_server* sv) {
             Done d{};
             st = collect(sv, i, &d);
             if (st) {
-                set_fatal(sv, st);
+                set_fatal(sv, st, ctx);
                 return;
             }
             d.status = gs[i].phase == kPhaseDone ? PG_OK
@@ -450,7 +495,7 @@ void worker_main(pg_server* sv) {
         }
         st = unpack_profiles(sv, keep);
         if (st) {
-            set_fatal(sv, st);
+            set_fatal(sv, st, ctx);
             return;
         }
         std::vector<Resident> rest;
@@ -459,10 +504,12 @@ void worker_main(pg_server* sv) {
             else free_game(sv->res[i].g);
         }
         sv->res.swap(rest);
+        sv->packed_count = 0;  // the kept profiles are out of the batch already
         changed = true;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             for (auto& f : fin) {
+                sv->inflight.erase(f.first);
                 sv->done[f.first] = std::move(f.second);
                 sv->done_order.push_back(f.first);
                 sv->stats.completed += 1;
@@ -510,7 +557,18 @@ pg_status pg_server_create(int device, const pg_server_opts* opts, pg_server** o
         delete sv;
         return st;
     }
+    st = pg_ctx_create(&sv->lctx, device);
+    if (st == PG_OK && cudaStreamCreateWithFlags(&sv->lctx->stream, cudaStreamNonBlocking) != cudaSuccess) st = PG_ECUDA;
+    if (st) {
+        if (sv->lctx) pg_ctx_destroy(sv->lctx);
+        free_game(sv->B);
+        cudaStreamDestroy(ctx->stream);
+        pg_ctx_destroy(ctx);
+        delete sv;
+        return st;
+    }
     sv->worker = std::thread(worker_main, sv);
+    sv->loader = std::thread(loader_main, sv);
     *out = sv;
     return PG_OK;
 }
@@ -522,13 +580,19 @@ void pg_server_destroy(pg_server* sv) {
         sv->stop = true;
     }
     sv->cv_work.notify_all();
+    sv->cv_load.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->loader.joinable()) sv->loader.join();
     cudaSetDevice(sv->ctx->device);
     cudaStreamSynchronize(sv->ctx->stream);
+    cudaStreamSynchronize(sv->lctx->stream);
     for (Resident& r : sv->res) free_game(r.g);
+    for (Resident& r : sv->ready) free_game(r.g);
     if (sv->B) free_game(sv->B);
     cudaStreamDestroy(sv->ctx->stream);
+    cudaStreamDestroy(sv->lctx->stream);
     pg_ctx_destroy(sv->ctx);
+    pg_ctx_destroy(sv->lctx);
     delete sv;
 }
 
@@ -551,10 +615,13 @@ pg_status pg_server_submit(pg_server* sv, int32_t n, int64_t m, const int32_t* o
         if (sv->done.count(tag)) return PG_EINVAL;
         for (const Pending& q : sv->queue)
             if (q.tag == tag) return PG_EINVAL;
+        for (const Resident& q : sv->ready)
+            if (q.tag == tag) return PG_EINVAL;
+        if (sv->inflight.count(tag)) return PG_EINVAL;
         sv->queue.push_back(std::move(p));
         sv->stats.submitted += 1;
     }
-    sv->cv_work.notify_all();
+    sv->cv_load.notify_all();
     return PG_OK;
 }
 
@@ -612,7 +679,7 @@ pg_status pg_server_get_stats(pg_server* sv, pg_server_stats* out) {
     if (!sv || !out) return PG_EINVAL;
     std::lock_guard<std::mutex> lk(sv->mu);
     *out = sv->stats;
-    out->queued = (int64_t)sv->queue.size();
+    out->queued = (int64_t)(sv->queue.size() + sv->ready.size());
     return PG_OK;
 }
 

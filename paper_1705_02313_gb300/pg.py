@@ -357,8 +357,14 @@ def pg_server_poll(server, max_results=64, timeout_ms=0):
     return [{f: getattr(buf[i], f) for f, _ in pg_served._fields_} for i in range(cnt.value)]
 
 
-def pg_server_fetch(server, tag, n, k):
-    """Results of a reported game as numpy arrays (and releases them)."""
+def pg_server_fetch(server, tag, n, k, keep=True):
+    """Results of a reported game as numpy arrays (and releases them); with
+    keep=False they are only released."""
+    if not keep:
+        rc = lib().pg_server_fetch(server, int(tag), *([None] * 7))
+        if rc != PG_OK:
+            raise PgError(rc, "pg_server_fetch")
+        return None
     out = dict(win=np.empty(n, np.uint8), sigma=np.empty(n, np.int32), tau=np.empty(n, np.int32),
                val_class=np.empty(n, np.int8), val_depth=np.empty(n, np.int32), val_rank=np.empty(n, np.int32),
                dummy_sigma=np.empty(max(k, 1), np.int8))
