@@ -126,22 +126,24 @@ class ClockSampler:
 # per-kernel algorithmic bytes (the compulsory traffic of each pass)
 
 def algorithmic_bytes(name, s):
+    """Compulsory bytes of one launch of a kernel class: every per-id array
+    read or written once at its element size, one gather per edge, chain and
+    walk steps beyond the first not counted (they are the kernels' own cost).
+    s: n = ids of G' (vertices, dummies, sink slot), m = edges, and the Odd /
+    Even split of both."""
     n, m = s["n"], s["m"]
-    if name == "walk":
-        return 12 * n
-    if name == "chain1":
-        return 15 * n
-    if name == "parents":
-        return 8 * n
-    if name == "sink_scan":
-        return 16 * n
-    if name == "chain2":
-        return 29 * n
-    if name == "switch_odd":
-        return n + 12 * s["n_odd"] + 8 * s["m_odd"]
-    if name == "switch_even":
-        return n + 16 * s["n_even"] + 8 * s["m_even"]
-    return None
+    table = {
+        "walk": 25 * n,        # strat 4 + flags 1 read; gd 8, gd32 4, size and odd-total zeros 8 written
+        "chain1": 15 * n,      # gd32 4 + flags 1 read; kind 1, cls 1, slot 4 written; one children-count atomic 4
+        "child_scan": 8 * n,   # counts read, offsets written
+        "scatter": 33 * n,     # kind 1, sz 4, gd32 4, slot 4, the parent's offset 4 read; entry 8, count 4, sink value 4 written
+        "siblings": 20 * n,    # offsets 4, entries 8 read; weight 4, odd total 4 written
+        "sink_scan": 16 * n,   # sink values read twice, weights written
+        "chain2": 17 * n,      # flags 1, odd total 4, weight 4, gd32 4 read; key 4 written
+        "switch_odd": n + 12 * s["n_odd"] + 8 * s["m_odd"],
+        "switch_even": n + 16 * s["n_even"] + 8 * s["m_even"],
+    }
+    return table.get(name)
 
 
 def kernel_source_hash():
