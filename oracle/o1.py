@@ -191,8 +191,11 @@ class NotAdmissible(Exception):
 
 def run(gp, strat=None, mode="solve", max_inner=10**6, trace=None):
     """Algorithm 1 (Section 4). mode "solve" runs both loops; mode
-    "best_response" runs the inner loop only. ``trace`` (a list) receives
-    (phase, strat, vals) after every valuation, for invariant checks."""
+    "best_response" runs the inner loop only; mode "solve_reset" runs both
+    loops but starts every best-response computation again from the initial
+    Odd strategy (the SI-Reset variant of Section 6). ``trace`` (a list)
+    receives (phase, strat, vals) after every valuation, for invariant
+    checks."""
     strat = initial_profile(gp) if strat is None else list(strat)
     major = inner = 0
     while True:
@@ -214,6 +217,9 @@ def run(gp, strat=None, mode="solve", max_inner=10**6, trace=None):
         if count == 0:
             break
         major += 1
+        if mode == "solve_reset":
+            init = initial_profile(gp)
+            strat = [init[v] if gp["own"][v] == 1 else strat[v] for v in range(gp["n"])]
     return result_of(gp, strat, vals, major, inner)
 
 
@@ -245,10 +251,10 @@ def map_back(gp, res):
     return dict(win=win, sigma=sigma, tau=tau, val_class=vc, val_depth=vd, val_rank=vr)
 
 
-def solve_game(n, off, tgt, own, pri):
-    """Convenience: preprocess, run Algorithm 1, map back."""
+def solve_game(n, off, tgt, own, pri, reset=False):
+    """Convenience: preprocess, run Algorithm 1 (SI-Reset with reset=True), map back."""
     gp = preprocess(n, list(off), list(tgt), list(own), list(pri))
-    res = run(gp)
+    res = run(gp, mode="solve_reset" if reset else "solve")
     out = map_back(gp, res)
     out.update(major=res["major"], inner=res["inner"])
     return gp, res, out

@@ -385,7 +385,10 @@ static int64_t o2_switch(const o2_game *g, int player, const int32_t *strat, int
  * with the greedy all-switches rule using the last inner valuation.
  * strat holds the initial profile on entry (callers pass sigma_init and the
  * first-edge tau for a cold start) and the final profile on exit.
- * mode 0: full solve; mode 1: best response only (inner loop).
+ * mode 0: full solve; mode 1: best response only (inner loop); mode 2: full
+ * solve in which every best-response computation starts again from the
+ * initial Odd strategy (the first edge of each list), the "SI-Reset" variant
+ * of Section 6.
  * stats (nullable): per inner iteration {n_fin, max_depth, sum_depth_lo32, n_odd_switch}.
  */
 int o2_run(int32_t n, const int32_t *off, const int32_t *tgt, const uint8_t *own, const int32_t *pri,
@@ -429,6 +432,9 @@ int o2_run(int32_t n, const int32_t *off, const int32_t *tgt, const uint8_t *own
         memcpy(strat, nstrat, sizeof(int32_t) * (size_t)n);
         if (nsw == 0) break;
         major++;
+        if (mode == 2)
+            for (int32_t v = 0; v < n; v++)
+                if (own[v]) strat[v] = tgt[off[v]];
     }
 done:
     *major_out = major;

@@ -75,9 +75,11 @@ def initial_profile(gp):
 
 
 def run(gp, strat=None, mode="solve", max_inner=10**9, check=False, stats_cap=0, allow_timeout=False):
-    """Algorithm 1 (Section 4) on the preprocessed game. Raises OracleError
-    for any non-OK status (except the iteration cap when ``allow_timeout``);
-    ``res['status']`` holds the status."""
+    """Algorithm 1 (Section 4) on the preprocessed game. mode: "solve",
+    "best_response" (inner loop only) or "solve_reset" (every best response
+    starts again from the initial Odd strategy: SI-Reset, Section 6). Raises
+    OracleError for any non-OK status (except the iteration cap when
+    ``allow_timeout``); ``res['status']`` holds the status."""
     n = gp["n"]
     strat = initial_profile(gp) if strat is None else np.array(strat, dtype=np.int32, copy=True)
     cls = np.zeros(n, np.int8)
@@ -89,7 +91,7 @@ def run(gp, strat=None, mode="solve", max_inner=10**9, check=False, stats_cap=0,
     inner = C.c_int64(0)
     stats = np.zeros(4 * max(stats_cap, 1), np.int64)
     rc = lib().o2_run(n, _p(gp["off"]), _p(gp["tgt"]), _p(gp["own"]), _p(gp["pri"]), _p(strat),
-                      0 if mode == "solve" else 1, int(max_inner), 1 if check else 0,
+                      {"solve": 0, "best_response": 1, "solve_reset": 2}[mode], int(max_inner), 1 if check else 0,
                       _p(cls), _p(depth), _p(rank), _p(dom), C.byref(sink_rank), C.byref(major), C.byref(inner),
                       _p(stats) if stats_cap else None, int(stats_cap))
     if rc and not (allow_timeout and rc == ETIMEOUT):
@@ -137,9 +139,10 @@ def map_back(gp, res):
                 val_depth=res["depth"][:n0].copy(), val_rank=res["rank"][:n0].copy())
 
 
-def solve_game(n, off, tgt, own, pri, check=False):
+def solve_game(n, off, tgt, own, pri, check=False, reset=False):
+    """Preprocess and solve; reset=True runs the SI-Reset variant (Section 6)."""
     gp = preprocess(n, off, tgt, own, pri)
-    res = run(gp, check=check)
+    res = run(gp, check=check, mode="solve_reset" if reset else "solve")
     out = map_back(gp, res)
     out.update(major=res["major"], inner=res["inner"])
     return gp, res, out

@@ -378,6 +378,25 @@ def test_o1_equals_o2(kind):
         assert (out1["major"], out1["inner"]) == (out2["major"], out2["inner"])
 
 
+def test_si_reset_same_major_iterations():
+    # SI-Reset (Section 6): every best response starts again from the initial
+    # Odd strategy. Best-response valuations are unique, so Even's switches,
+    # hence the major iterations, sigma, the winners and the final valuations
+    # do not depend on it (the paper reports the same major iterations); the
+    # two oracle tiers agree on the reset run, inner iterations included.
+    for s in range(10):
+        g = gen.random_game(30 + 29 * s, 1, 5, seed=900 + s) if s % 3 else gen.ladder_game(40 + 13 * s, seed=s)
+        _, r1, a1 = o1.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri, reset=True)
+        _, r2, a2 = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri, check=True, reset=True)
+        for k in OUT_KEYS:
+            assert np.array_equal(np.asarray(a1[k]), np.asarray(a2[k])), (s, k)
+        assert (a1["major"], a1["inner"]) == (a2["major"], a2["inner"])
+        _, _, b = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
+        assert a2["major"] == b["major"] and a2["inner"] >= b["inner"]
+        for k in ["win", "sigma", "val_class", "val_depth", "val_rank"]:
+            assert np.array_equal(np.asarray(a2[k]), np.asarray(b[k])), (s, k)
+
+
 def test_o2_config_small_reference_run():
     # the 1,000-vertex random workload (out-degree U[1,4], seed 0) end to end
     g = gen.random_game(1000, 1, 4, 0)
