@@ -528,6 +528,19 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if rank == 0:  # ablation of Section 6 (Table 2): best responses restarted from the initial Odd strategy
+        g = pg.pg_load_csr(ctx, n, m, *d_in)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r_major, r_inner = pg.pg_solve(ctx, g, win=out["win"], reset_tau=True)
+            torch.cuda.synchronize()
+            r_ms = (time.perf_counter() - t0) * 1e3
+        finally:
+            pg.pg_game_free(g)
+        line["si_reset"] = {"major_iterations": r_major, "valuations": r_inner, "solve_ms": r_ms,
+                            "valuations_plain": inner, "major_plain": major,
+                            "note": "SI-Reset: every best response restarts from the first edge of each Odd list"}
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_measure(args.batch)
     if rank == 0 and args.serve > 0:

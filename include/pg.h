@@ -86,6 +86,9 @@ typedef struct {
     const int8_t *dummy_sigma_init;/* nullable: k entries, as in pg_result */
     int32_t mem_kind;              /* where the warm-start arrays live */
     int64_t max_inner;             /* cap on valuations computed; 0 = 64 * (n' + 64) */
+    int32_t reset_tau;             /* 1: SI-Reset (Section 6): after every Even switch the inner loop starts
+                                      again from the initial Odd strategy (the first edge of each list of G')
+                                      instead of the last best response; same major iterations, more inner */
 } pg_solve_opts;
 
 /* Valuation of one profile. Caller-owned arrays of n entries; NULL skips. */

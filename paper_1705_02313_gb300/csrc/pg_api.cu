@@ -270,6 +270,7 @@ pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
     if (!st) st = enqueue_switch(g, 1);
     if (!st && even) st = enqueue_switch(g, 0);
     if (!st) st = enqueue_bookkeeping(g, cap, even);
+    if (!st && even && g->reset_tau) st = enqueue_reset(g);
     return st;
 }
 
@@ -279,7 +280,8 @@ pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
 bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     const int w = even ? 1 : 0;
-    if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit) return true;
+    if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit && g->loop_reset[w] == g->reset_tau)
+        return true;
     if (g->loop_exec[w]) {
         cudaGraphExecDestroy(g->loop_exec[w]);
         g->loop_exec[w] = nullptr;
@@ -343,6 +345,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     }
     g->loop_cap[w] = cap;
     g->loop_limit[w] = limit;
+    g->loop_reset[w] = g->reset_tau;
     return true;
 }
 
@@ -386,6 +389,7 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
         st = enqueue_switch(g, 1);
         if (!st && even) st = enqueue_switch(g, 0);
         if (!st) st = enqueue_bookkeeping(g, cap, even);
+        if (!st && even && g->reset_tau) st = enqueue_reset(g);
         if (st) return st;
         tm.mark(2);
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinned, g->gactive, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -531,7 +535,9 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     if (st) return st;
     Timer tm(g);
     tm.mark(3);
+    g->reset_tau = opts && opts->reset_tau;
     st = run_loop(g, cap, true, tm);
+    g->reset_tau = false;
     if (st) return st;
     GameState gs;
     PG_CUDA_TRY(ctx, cudaMemcpy(&gs, g->gst, sizeof(gs), cudaMemcpyDeviceToHost));

@@ -126,6 +126,7 @@ struct GameState {
     int32_t sw_odd;   // Odd switches in this iteration
     int32_t sw_even;  // Even switches in this iteration
     int32_t nodd;     // vertices reaching an odd cycle in this iteration's valuation
+    int32_t reset;    // Even switched and Odd restarts from its initial strategy (SI-Reset, Section 6)
     int64_t inner;    // valuations computed
     int64_t major;    // Even switching rounds that switched something
 };
@@ -198,6 +199,8 @@ struct pg_game {
     int64_t loop_launch[2] = {0, 0};                  // kernels per iteration of each graph
     int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
     bool last_graph = false;     // the last loop ran as a graph
+    bool reset_tau = false;      // SI-Reset (Section 6): Odd restarts from its first edges after every Even switch
+    bool loop_reset[2] = {false, false};  // the SI-Reset setting each loop graph was built with
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;
@@ -253,6 +256,8 @@ void drop_loop_graphs(pg_game* g);
 pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out);
 // Per-game loop bookkeeping after the switching passes; counts active games.
 pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase);
+// SI-Reset: Odd vertices of games whose Even player just switched back to their first edge.
+pg_status enqueue_reset(pg_game* g);
 // Resets the per-game state for a new solve.
 pg_status reset_games(pg_game* g);
 void free_game(pg_game* g);

@@ -992,16 +992,22 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
 // per game): count the valuation, stop at an odd cycle, finish when neither
 // player switched (or, for best responses, when Odd did not), count a major
 // iteration when Even switched, stop at the cap. Counts the games still active.
-__global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even_phase, int32_t* gactive) {
+// With reset_mode, a game whose Even player switched is marked for k_reset_odd.
+__global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even_phase, int reset_mode,
+                           int32_t* gactive) {
     int32_t act = 0;
     for (int32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngames; gi += gridDim.x * blockDim.x) {
         GameState st = gst[gi];
+        st.reset = 0;
         if (st.phase == kPhaseActive) {
             st.inner += 1;
             if (st.nodd > 0) st.phase = kPhaseOddCycle;
             else if (st.sw_odd == 0) {
                 if (!even_phase || st.sw_even == 0) st.phase = kPhaseDone;
-                else st.major += 1;
+                else {
+                    st.major += 1;
+                    st.reset = reset_mode;
+                }
             }
             if (st.phase == kPhaseActive && st.inner >= cap) st.phase = kPhaseTimeout;
         }
@@ -1010,6 +1016,23 @@ __global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even
         act += st.phase == kPhaseActive;
     }
     block_add(act, gactive);
+}
+
+// SI-Reset (Section 6): in games marked by k_bookkeep, every Odd vertex goes
+// back to the first edge of its list (the initial strategy of Algorithm 1).
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_reset_odd(int32_t n, const OffT* __restrict__ off,
+                                                      const int32_t* __restrict__ tgt,
+                                                      const uint8_t* __restrict__ flags,
+                                                      const int32_t* __restrict__ vgame, const GameState* gst,
+                                                      int32_t* strat) {
+    if (!vgame && !gst[0].reset) return;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        if ((f & kSinkSlot) || !(f & kOwnerOdd)) continue;
+        if (vgame && !gst[vgame[v]].reset) continue;
+        strat[v] = tgt[off[v]];
+    }
 }
 
 }  // namespace
@@ -1190,7 +1213,21 @@ pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gactive, 0, sizeof(int32_t), s));
     ctx->launches += 1;
     const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + kBlock - 1) / kBlock, 1024));
-    k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->gactive);
+    k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->reset_tau ? 1 : 0, g->gactive);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_reset(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    ctx->launches += 1;
+    if (g->off64)
+        k_reset_odd<int64_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, g->off64, g->tgt, g->flags, g->vgame, g->gst,
+                                                               g->strat);
+    else
+        k_reset_odd<int32_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, g->off, g->tgt, g->flags, g->vgame, g->gst,
+                                                               g->strat);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }

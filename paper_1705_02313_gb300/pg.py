@@ -42,7 +42,7 @@ class pg_result(C.Structure):
 
 class pg_solve_opts(C.Structure):
     _fields_ = [("sigma_init", C.c_void_p), ("tau_init", C.c_void_p), ("dummy_sigma_init", C.c_void_p),
-                ("mem_kind", C.c_int32), ("max_inner", C.c_int64)]
+                ("mem_kind", C.c_int32), ("max_inner", C.c_int64), ("reset_tau", C.c_int32)]
 
 
 class pg_valuation(C.Structure):
@@ -240,7 +240,7 @@ def pg_game_dummies(game):
 
 
 def pg_solve(ctx, game, win=None, sigma=None, tau=None, val_class=None, val_depth=None, val_rank=None,
-             dummy_sigma=None, sigma_init=None, tau_init=None, dummy_sigma_init=None, max_inner=0):
+             dummy_sigma=None, sigma_init=None, tau_init=None, dummy_sigma_init=None, max_inner=0, reset_tau=False):
     """Fills the given output arrays (all in host memory or all in device
     memory); returns (major, inner)."""
     _dtype_check(win, np.uint8, "win")
@@ -252,7 +252,7 @@ def pg_solve(ctx, game, win=None, sigma=None, tau=None, val_class=None, val_dept
                     _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dummy_sigma)[0],
                     _same_kind(win, sigma, tau, val_class, val_depth, val_rank, dummy_sigma), 0, 0)
     opts = pg_solve_opts(_ptr_kind(sigma_init)[0], _ptr_kind(tau_init)[0], _ptr_kind(dummy_sigma_init)[0],
-                         _same_kind(sigma_init, tau_init, dummy_sigma_init), int(max_inner))
+                         _same_kind(sigma_init, tau_init, dummy_sigma_init), int(max_inner), 1 if reset_tau else 0)
     rc = lib().pg_solve(game, C.byref(opts), C.byref(res))
     _check(ctx, rc, "pg_solve")
     return res.major, res.inner

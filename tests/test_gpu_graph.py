@@ -137,3 +137,25 @@ def test_graph_best_response_and_batch(pg, ctx):
     assert np.array_equal(rg["inner"], rh["inner"]) and np.array_equal(rg["major"], rh["major"])
     for key in og:
         assert np.array_equal(og[key], oh[key])
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_si_reset_matches_oracle(pg, ctx, graphs):
+    # SI-Reset (Section 6): every best response restarts from the first edges
+    pg.pg_set_graphs(ctx, graphs)
+    for g in [gen.random_game(2000, 1, 5, 31), gen.random_game(15000, 2, 6, 32), gen.ladder_game(3000, 33)]:
+        game = pg.pg_load_csr(ctx, g.n, g.m, *g.arrays())
+        try:
+            _, _, k = pg.pg_game_info(game)
+            out = host_outputs(g.n, k)
+            major, inner = pg.pg_solve(ctx, game, reset_tau=True, **out)
+            assert pg.pg_last_loop(game)[0] == graphs
+            plain = host_outputs(g.n, k)
+            major0, inner0 = pg.pg_solve(ctx, game, **plain)
+        finally:
+            pg.pg_game_free(game)
+        _, _, want = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri, reset=True)
+        for key in KEYS:
+            assert np.array_equal(out[key], np.asarray(want[key])), key
+        assert (major, inner) == (want["major"], want["inner"])
+        assert major == major0 and inner >= inner0
