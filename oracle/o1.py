@@ -47,12 +47,17 @@ def odd_trap(n, off, tgt, own):
     return U
 
 
-def preprocess(n, off, tgt, own, pri):
+def preprocess(n, off, tgt, own, pri, dummy_zero=None):
     """Builds G' from G: for each w in U that some edge from U enters (W, in
     increasing id order), dummy vertex n + j (j = index of w in W) is an Even
     vertex of priority 2j with the single edge to w; edges U -> w are
-    redirected to it; every original priority p becomes p + 2|W|. Returns a
-    dict with the new CSR arrays as Python lists plus ``dummy_of`` and ``k``."""
+    redirected to it; every original priority p becomes p + 2|W|. When the
+    priorities repeat (or dummy_zero is set) every dummy gets priority 0 and
+    every original priority p becomes p + 2 instead, so that the dummies add
+    one priority rather than |W|. Returns a dict with the new CSR arrays as
+    Python lists plus ``dummy_of`` and ``k``."""
+    if dummy_zero is None:
+        dummy_zero = len(set(int(p) for p in pri)) < n
     U = odd_trap(n, off, tgt, own)
     W = sorted({int(tgt[e]) for v in U for e in range(off[v], off[v + 1]) if int(tgt[e]) in U})
     k = len(W)
@@ -64,13 +69,14 @@ def preprocess(n, off, tgt, own, pri):
             ntgt.append(n + index[t] if (v in U and t in U) else t)
         noff.append(len(ntgt))
         nown.append(int(own[v]))
-        npri.append(int(pri[v]) + 2 * k)
+        npri.append(int(pri[v]) + (2 if dummy_zero else 2 * k))
     for j, w in enumerate(W):
         ntgt.append(w)
         noff.append(len(ntgt))
         nown.append(0)
-        npri.append(2 * j)
-    return dict(n=n + k, off=noff, tgt=ntgt, own=nown, pri=npri, dummy_of=W, k=k, U=U, n_orig=n)
+        npri.append(0 if dummy_zero else 2 * j)
+    return dict(n=n + k, off=noff, tgt=ntgt, own=nown, pri=npri, dummy_of=W, k=k, U=U, n_orig=n,
+                dummy_zero=bool(dummy_zero))
 
 
 # ---------------------------------------------------------------------------
@@ -181,8 +187,12 @@ def result_of(gp, strat, vals, major, inner):
     cls = [vals[v][0] for v in range(gp["n"])]
     depth = [sum(vals[v][1].values()) if vals[v][0] == FIN else -1 for v in range(gp["n"])]
     dom = [vals[v][2] for v in range(gp["n"])]
+    # count vectors over the distinct priorities of G' in ascending order (zeros for top)
+    level_pri = sorted(set(gp["pri"]))
+    counts = [[vals[v][1].get(p, 0) for p in level_pri] if vals[v][0] == FIN else [0] * len(level_pri)
+              for v in range(gp["n"])]
     return dict(strat=list(strat), cls=cls, depth=depth, rank=rank, sink_rank=sink_rank, dom=dom,
-                major=major, inner=inner)
+                major=major, inner=inner, counts=counts, level_pri=level_pri)
 
 
 class NotAdmissible(Exception):

@@ -60,12 +60,16 @@ typedef struct {
  * that is the target of an edge from U gets a dummy Even vertex d_w with the
  * single edge d_w -> w; edges U -> w are redirected to d_w. Dummy j (for the
  * j-th such w in increasing id order) has id n+j and priority 2j; every
- * original priority p becomes p + 2k. Outputs must be sized for the worst
- * case: out_off[2n+1], out_tgt[m+n], out_own[2n], out_pri[2n], dummy_of[n].
+ * original priority p becomes p + 2k. With dummy_zero (games whose
+ * priorities repeat, ranked by count vectors) every dummy has priority 0
+ * instead and every original priority becomes p + 2: the dummies then add
+ * one priority, not k. Both keep parities and put the dummies below every
+ * original priority. Outputs must be sized for the worst case:
+ * out_off[2n+1], out_tgt[m+n], out_own[2n], out_pri[2n], dummy_of[n].
  */
 int o2_preprocess(int32_t n, const int32_t *off, const int32_t *tgt, const uint8_t *own,
                   const int32_t *pri, int32_t *out_off, int32_t *out_tgt, uint8_t *out_own,
-                  int32_t *out_pri, int32_t *dummy_of, int32_t *k_out, uint8_t *in_u_out)
+                  int32_t *out_pri, int32_t *dummy_of, int32_t *k_out, uint8_t *in_u_out, int dummy_zero)
 {
     int64_t m = off[n];
     /* count, for every Odd vertex, its edges into the current U (initially all Odd) */
@@ -132,14 +136,14 @@ int o2_preprocess(int32_t n, const int32_t *off, const int32_t *tgt, const uint8
         }
         out_off[v + 1] = base + (off[v + 1] - off[v]);
         out_own[v] = own[v];
-        out_pri[v] = pri[v] + 2 * k;
+        out_pri[v] = pri[v] + (dummy_zero ? 2 : 2 * k);
     }
     for (int32_t j = 0; j < k; j++) {
         int32_t d = n + j;
         out_tgt[out_off[d]] = dummy_of[j];
         out_off[d + 1] = out_off[d] + 1;
         out_own[d] = 0;
-        out_pri[d] = 2 * j;
+        out_pri[d] = dummy_zero ? 0 : 2 * j;
     }
     (void)np_;
     if (in_u_out) memcpy(in_u_out, inU, (size_t)n);

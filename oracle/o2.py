@@ -23,7 +23,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(_build.build())
         P = C.c_void_p
-        _lib.o2_preprocess.argtypes = [C.c_int32, P, P, P, P, P, P, P, P, P, P, P]
+        _lib.o2_preprocess.argtypes = [C.c_int32, P, P, P, P, P, P, P, P, P, P, P, C.c_int]
         _lib.o2_run.argtypes = [C.c_int32, P, P, P, P, P, C.c_int, C.c_int64, C.c_int,
                                 P, P, P, P, P, P, P, P, C.c_int64]
         _lib.o2_valuate_profile.argtypes = [C.c_int32, P, P, P, P, P, P, P]
@@ -41,9 +41,11 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def preprocess(n, off, tgt, own, pri):
+def preprocess(n, off, tgt, own, pri, dummy_zero=None):
     """P0 of Section 3 (see ``o2_preprocess``). Returns a dict of numpy
-    arrays for G' plus ``dummy_of``, ``k`` and ``inU``."""
+    arrays for G' plus ``dummy_of``, ``k`` and ``inU``. dummy_zero (default:
+    when priorities repeat) gives every dummy priority 0 and shifts original
+    priorities by 2, instead of priorities 2j and a shift of 2k."""
     off = np.ascontiguousarray(off, dtype=np.int32)
     tgt = np.ascontiguousarray(tgt, dtype=np.int32)
     own = np.ascontiguousarray(own, dtype=np.uint8)
@@ -56,15 +58,18 @@ def preprocess(n, off, tgt, own, pri):
     dummy = np.zeros(max(n, 1), np.int32)
     inU = np.zeros(max(n, 1), np.uint8)
     k = C.c_int32(0)
+    if dummy_zero is None:
+        dummy_zero = np.unique(pri).size < n
     rc = lib().o2_preprocess(n, _p(off), _p(tgt), _p(own), _p(pri), _p(o_off), _p(o_tgt), _p(o_own),
-                             _p(o_pri), _p(dummy), C.byref(k), _p(inU))
+                             _p(o_pri), _p(dummy), C.byref(k), _p(inU), 1 if dummy_zero else 0)
     if rc:
         raise OracleError(rc, "o2_preprocess")
     k = k.value
     np_ = n + k
     mp = int(o_off[np_])
     return dict(n=np_, n_orig=n, k=k, off=o_off[: np_ + 1].copy(), tgt=o_tgt[:mp].copy(),
-                own=o_own[:np_].copy(), pri=o_pri[:np_].copy(), dummy_of=dummy[:k].copy(), inU=inU[:n].copy())
+                own=o_own[:np_].copy(), pri=o_pri[:np_].copy(), dummy_of=dummy[:k].copy(), inU=inU[:n].copy(),
+                dummy_zero=bool(dummy_zero))
 
 
 def initial_profile(gp):

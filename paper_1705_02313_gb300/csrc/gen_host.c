@@ -298,8 +298,9 @@ static void* range_worker(void* p) {
     return NULL;
 }
 
+/* levels > 0: priorities uniform over 0 .. levels-1 instead of a permutation. */
 int pggen_fill_game(int64_t n, int64_t dmin, int64_t dmax, uint64_t seed, uint64_t owner_thr, int32_t* offsets,
-                    int32_t* targets, uint8_t* owner, int32_t* pri, int nthreads) {
+                    int32_t* targets, uint8_t* owner, int32_t* pri, int nthreads, int64_t levels) {
     if (n < 1 || n >= ((int64_t)1 << 31) || dmin < 1 || dmax < dmin || dmax > 64) return -1;
     game_spec s = make_spec(n, dmin, dmax, seed);
     const uint64_t kdeg = stream_key(seed, S_DEGREE);
@@ -328,7 +329,13 @@ int pggen_fill_game(int64_t n, int64_t dmin, int64_t dmax, uint64_t seed, uint64
     for (int t = 1; t < nthreads; ++t)
         if (!created[t]) range_worker(&R[t]);
     /* priorities (one sort) on this thread while the workers fill edges */
-    const int perr = fill_priorities(&s, pri);
+    int perr = 0;
+    if (levels > 0) {
+        const uint64_t kp = stream_key(seed, S_PRIORITY);
+        for (int64_t v = 0; v < n; ++v) pri[v] = (int32_t)below(draw_k(kp, (uint64_t)v, 0), (uint64_t)levels);
+    } else {
+        perr = fill_priorities(&s, pri);
+    }
     range_worker(&R[0]);
     for (int t = 1; t < nthreads; ++t)
         if (created[t]) pthread_join(th[t], NULL);

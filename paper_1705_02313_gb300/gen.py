@@ -130,10 +130,16 @@ def _csr_from_degrees(deg):
     return off.astype(np.int32)
 
 
-def random_game(n, dmin, dmax, seed=0, p_odd=0.5):
+def level_priorities(n, levels, seed):
+    """Priorities drawn uniformly from 0..levels-1 (few distinct priorities,
+    as in the verification games the paper measures)."""
+    return uniform_below(draw(seed, S_PRIORITY, np.arange(n, dtype=np.uint64), 0), levels).astype(np.int32)
+
+
+def random_game(n, dmin, dmax, seed=0, p_odd=0.5, levels=0):
     """Random game: out-degree uniform in [dmin, dmax] (capped at n), distinct
     uniform targets, owner Odd with probability p_odd, priorities a random
-    permutation of 0..n-1."""
+    permutation of 0..n-1 (levels = 0) or uniform over 0..levels-1."""
     if n <= 0:
         raise ValueError("n must be positive")
     dmin, dmax = min(dmin, n), min(dmax, n)
@@ -141,7 +147,8 @@ def random_game(n, dmin, dmax, seed=0, p_odd=0.5):
     deg = (dmin + uniform_below(draw(seed, S_DEGREE, v, 0), dmax - dmin + 1)).astype(np.int64)
     off = _csr_from_degrees(deg)
     tgt = _distinct_targets(n, deg, seed)
-    return Game(n, off, tgt, random_owners(n, seed, p_odd), permuted_priorities(n, seed))
+    pri = level_priorities(n, levels, seed) if levels else permuted_priorities(n, seed)
+    return Game(n, off, tgt, random_owners(n, seed, p_odd), pri)
 
 
 def ladder_game(n, seed=0, p_odd=0.5):
@@ -242,7 +249,7 @@ def _gen_lib():
         lib.pggen_fill_batch.argtypes = [i64, i64p, u64p, i64, i64, ctypes.c_uint64, i64p, i64p, vp, vp, vp, vp,
                                          ctypes.c_int]
         lib.pggen_fill_game.argtypes = [i64, i64, i64, ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp,
-                                        ctypes.c_int]
+                                        ctypes.c_int, i64]
         _GEN = lib
     return _GEN
 
@@ -259,8 +266,8 @@ def _addr(x):
     return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
 
 
-def native_random_game(n, dmin, dmax, seed=0, p_odd=0.5, nthreads=0):
-    """random_game(n, dmin, dmax, seed, p_odd), generated by the C generator."""
+def native_random_game(n, dmin, dmax, seed=0, p_odd=0.5, nthreads=0, levels=0):
+    """random_game(n, dmin, dmax, seed, p_odd, levels), generated by the C generator."""
     lib = _gen_lib()
     sizes = np.array([n], np.int64)
     seeds = np.array([seed], np.uint64)
@@ -275,7 +282,7 @@ def native_random_game(n, dmin, dmax, seed=0, p_odd=0.5, nthreads=0):
     own = np.empty(n, np.uint8)
     pri = np.empty(n, np.int32)
     if lib.pggen_fill_game(n, dmin, dmax, seed, _owner_threshold(p_odd), off.ctypes.data, tgt.ctypes.data,
-                           own.ctypes.data, pri.ctypes.data, _threads(nthreads)):
+                           own.ctypes.data, pri.ctypes.data, _threads(nthreads), levels):
         raise ValueError("generator failed")
     return Game(n, off, tgt, own, pri)
 
