@@ -46,6 +46,9 @@ WORKLOADS = {
                   "(profiling case: inputs above L2, about 1 GB on the device)"),
     "ladder-10m": ("ladder_game", dict(n=10_000_000, seed=0),
                    "ladder game, n=10,000,000, i->i+1 plus one back edge, owners p=0.5, permuted priorities"),
+    "random-10m-4pri": ("random_game", dict(n=10_000_000, dmin=2, dmax=5, seed=0, levels=4),
+                        "random game, n=10,000,000, out-degree U[2,5], owners p=0.5, priorities uniform over 0..3 "
+                        "(count-vector mode; the shape of the verification games of Table 1)"),
 }
 
 
@@ -54,7 +57,7 @@ def make_game(name):
     fn, kw, _ = WORKLOADS[name]
     kw = dict(kw)
     if fn == "random_game":  # the C generator: the same game as gen.random_game
-        return gen.native_random_game(kw["n"], kw["dmin"], kw["dmax"], kw["seed"])
+        return gen.native_random_game(kw["n"], kw["dmin"], kw["dmax"], kw["seed"], levels=kw.get("levels", 0))
     return gen.ladder_game(kw["n"], kw["seed"])
 
 
@@ -167,6 +170,48 @@ def measured_traffic(kernel, workload):
         return e["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+# ---------------------------------------------------------------------------
+# count-vector mode: games whose priorities repeat
+
+def cv_measure(name, ctx, steps=3):
+    """Full solves of a repeated-priority workload: one warm-up, then steps
+    solves (load + solve from device arrays, results to device), CUDA events."""
+    import torch
+
+    from paper_1705_02313_gb300 import pg
+    game = make_game(name)
+    n, m = game.n, game.m
+    d_in = [torch.from_numpy(a).cuda() for a in game.arrays()]
+    win = torch.empty(n, dtype=torch.uint8, device="cuda")
+    levels = None
+
+    def one():
+        nonlocal levels
+        g = pg.pg_load_csr(ctx, n, m, *d_in)
+        try:
+            levels = pg.pg_game_levels(g)
+            cnt = torch.empty(n * max(levels.size, 1), dtype=torch.int32, device="cuda")
+            return pg.pg_solve(ctx, g, win=win, val_counts=cnt)
+        finally:
+            pg.pg_game_free(g)
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    inner_total = 0
+    for _ in range(steps):
+        major, inner = one()
+        inner_total += inner
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": name, "description": WORKLOADS[name][2], "n": n, "m": m, "levels_of_g_prime": levels.tolist(),
+            "major_iterations": major, "valuations_per_solve": inner, "full_solve_ms": ms,
+            "edges_per_s": m * inner_total / (ms * steps / 1000.0), "unit": "edges/s",
+            "inner_iteration_us": ms * 1000.0 / inner}
 
 
 # ---------------------------------------------------------------------------
@@ -541,6 +586,8 @@ def run_ours(args):
         line["si_reset"] = {"major_iterations": r_major, "valuations": r_inner, "solve_ms": r_ms,
                             "valuations_plain": inner, "major_plain": major,
                             "note": "SI-Reset: every best response restarts from the first edge of each Odd list"}
+    if rank == 0 and args.cv_workload:
+        line["count_vector"] = cv_measure(args.cv_workload, ctx)
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_measure(args.batch)
     if rank == 0 and args.serve > 0:
@@ -601,6 +648,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-one-at-a-time measurement")
+    ap.add_argument("--cv-workload", default="random-10m-4pri",
+                    help="count-vector workload measured beside the main line ('' to skip)")
     ap.add_argument("--serve", type=float, default=10.0,
                     help="seconds of the Poisson serving stream measured beside the main line (0: skip)")
     ap.add_argument("--batch", choices=sorted(BATCHES), default="batch-256",

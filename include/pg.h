@@ -9,9 +9,11 @@
  *  - Games are CSR int32: offsets[n+1] (offsets[0] = 0, non-decreasing,
  *    offsets[n] = m), targets[m] in [0, n), owner[n] (0 = Even, 1 = Odd),
  *    pri[n] >= 0. Every vertex has at least one out-edge (Section 2: no
- *    terminal vertices). This version requires pairwise distinct priorities,
- *    the regime of the measured workloads (permuted priorities); a repeated
- *    priority is rejected with PG_EUNSUPPORTED.
+ *    terminal vertices). Pairwise distinct priorities (the random workloads'
+ *    permuted priorities) are ranked by the nearest-greater forest; a game
+ *    whose priorities repeat runs in count-vector mode (below), which needs
+ *    at most 5 distinct priorities after preprocessing and fewer than 2^24
+ *    vertices, else PG_EUNSUPPORTED.
  *  - mem_kind says where caller arrays live: PG_MEM_HOST (pageable or pinned
  *    host memory) or PG_MEM_DEVICE (device memory of the context's GPU).
  *    Caller arrays are read or written during the call only and never
@@ -36,6 +38,16 @@
  *              the empty valuation of the sink, counted from 0; INT32_MAX for
  *              TOP.
  * Together with the strategies these determine every count vector exactly.
+ *
+ * Count-vector mode (games whose priorities repeat, as the verification games
+ * the paper measures: Section 6, Table 1): the preprocessing gives every
+ * dummy priority 0 and adds 2 to every original priority (so the dummies add
+ * one priority, not k). A finite valuation is the count vector L(p) of
+ * Section 3 over the d distinct priorities of G' (pg_game_levels lists them
+ * in ascending order); val_counts receives it as n rows of d counts (zeros
+ * for TOP); val_rank is -1 in this mode (equal valuations exist); val_class
+ * and val_depth are as above. Batches and servers take distinct priorities
+ * only.
  */
 #ifndef PG_H
 #define PG_H
@@ -77,6 +89,7 @@ typedef struct {
     int32_t mem_kind;    /* where the arrays above live */
     int64_t major;       /* out: outer iterations that switched Even's strategy */
     int64_t inner;       /* out: valuations computed (total inner iterations) */
+    int32_t *val_counts; /* count-vector mode only: n x d counts (row per vertex); ignored otherwise */
 } pg_result;
 
 /* Options of pg_solve; pass NULL for the defaults. */
@@ -98,6 +111,7 @@ typedef struct {
     int32_t *val_rank;
     int32_t *dom;        /* TOP vertices: largest priority on the cycle reached; -1 if finite */
     int32_t mem_kind;
+    int32_t *val_counts; /* count-vector mode only: n x d counts (row per vertex); ignored otherwise */
 } pg_valuation;
 
 /* Context: one GPU, one stream. device is the CUDA ordinal. */
@@ -128,6 +142,11 @@ void pg_game_free(pg_game *game);
 pg_status pg_game_info(const pg_game *game, int32_t *n, int64_t *m, int32_t *k);
 
 /* The vertex each dummy guards: out[j] = w for dummy j (k entries, host memory). */
+/* Count-vector mode: *d receives the number of distinct priorities of G'
+ * (0 for a game with distinct priorities) and level_pri (nullable, d <= 5
+ * entries) their values in G' (original priority + 2; 0 for the dummies), in
+ * ascending order: column l of val_counts counts level_pri[l]. */
+pg_status pg_game_levels(const pg_game *game, int32_t *d, int32_t *level_pri);
 pg_status pg_game_dummies(const pg_game *game, int32_t *out);
 
 /* Full solve: Algorithm 1 (Section 4) from sigma_init (every Even vertex to

@@ -36,7 +36,7 @@ void free_game(pg_game* g) {
                     g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
-                    g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters};
+                    g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->hcnt) cudaFreeHost(g->hcnt);
@@ -105,6 +105,7 @@ __global__ void k_apply_profile(int64_t n0, int32_t k, const int32_t* __restrict
 }
 
 struct OutPtrs {
+    int32_t cv;  // count-vector mode: valuations are count vectors, there is no rank (written as -1)
     uint8_t* win;
     int32_t* sigma;
     int32_t* tau;
@@ -139,7 +140,7 @@ __global__ void k_results(int64_t n0, int32_t k, const int32_t* __restrict__ nid
         if (o.tau) o.tau[v] = odd ? orig_of[s] : -1;
         if (o.vclass) o.vclass[v] = fin ? 0 : 1;
         if (o.vdepth) o.vdepth[v] = fin ? depth[i] : -1;
-        if (o.vrank) o.vrank[v] = fin ? key[i] : INT32_MAX;
+        if (o.vrank) o.vrank[v] = o.cv ? -1 : (fin ? key[i] : INT32_MAX);
         if (o.vdom) o.vdom[v] = dom[i];
     }
 }
@@ -170,12 +171,13 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
                         int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig, bool depth_ready) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
-    OutPtrs o = {win, sigma, tau, vclass, vdepth, vrank, vdom, dsig};
+    OutPtrs o = {g->cv ? 1 : 0, win, sigma, tau, vclass, vdepth, vrank, vdom, dsig};
     Stage L = stage_layout(g->n0, g->k);
     if (mem_kind == PG_MEM_HOST) {
         if (!g->stage) PG_CUDA_TRY(ctx, cudaMalloc(&g->stage, L.bytes));
         char* b = (char*)g->stage;
-        o = {win ? (uint8_t*)(b + L.off_win) : nullptr,     sigma ? (int32_t*)(b + L.off_sigma) : nullptr,
+        o = {g->cv ? 1 : 0,
+             win ? (uint8_t*)(b + L.off_win) : nullptr,     sigma ? (int32_t*)(b + L.off_sigma) : nullptr,
              tau ? (int32_t*)(b + L.off_tau) : nullptr,     vclass ? (int8_t*)(b + L.off_class) : nullptr,
              vdepth ? (int32_t*)(b + L.off_depth) : nullptr, vrank ? (int32_t*)(b + L.off_rank) : nullptr,
              vdom ? (int32_t*)(b + L.off_dom) : nullptr,     dsig ? (int8_t*)(b + L.off_dsig) : nullptr};
@@ -516,6 +518,14 @@ pg_status pg_game_info(const pg_game* g, int32_t* n, int64_t* m, int32_t* k) {
     return PG_OK;
 }
 
+pg_status pg_game_levels(const pg_game* g, int32_t* d, int32_t* level_pri) {
+    if (!g || !d) return PG_EINVAL;
+    *d = g->cv ? g->lev.n : 0;
+    if (level_pri && g->cv)
+        for (int32_t l = 0; l < g->lev.n; ++l) level_pri[l] = g->lev_pri[l];
+    return PG_OK;
+}
+
 pg_status pg_game_dummies(const pg_game* g, int32_t* out) {
     if (!g || (!out && g->k)) return PG_EINVAL;
     if (g->k == 0) return PG_OK;
@@ -555,6 +565,7 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     out->inner = gs.inner;
     st = write_outputs(g, out->mem_kind, out->win, out->sigma, out->tau, out->val_class, out->val_depth,
                        out->val_rank, nullptr, out->dummy_sigma);
+    if (!st && g->cv && out->val_counts) st = write_counts(g, out->mem_kind, out->val_counts);
     if (st) return st;
     if (timed_out) return fail(ctx, PG_ETIMEOUT, "pg_solve: iteration cap reached");
     return PG_OK;
@@ -586,6 +597,7 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
     if (out) {
         st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, out->val_class, out->val_depth,
                            out->val_rank, nullptr, nullptr);
+        if (!st && g->cv && out->val_counts) st = write_counts(g, out->mem_kind, out->val_counts);
         if (st) return st;
         if (out->dom) {
             // dom needs a valuation that records it
@@ -621,6 +633,7 @@ pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma
     if (out) {
         st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, out->val_class, out->val_depth, out->val_rank,
                            out->dom, nullptr);
+        if (!st && g->cv && out->val_counts) st = write_counts(g, out->mem_kind, out->val_counts);
         if (st) return st;
     }
     if (g->hcnt->n_odd > 0) return fail(ctx, PG_ENOTADMISSIBLE, "pg_valuate: the profile reaches an odd cycle");

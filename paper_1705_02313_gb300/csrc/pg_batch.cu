@@ -169,6 +169,10 @@ pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int6
             cleanup();
             return st;
         }
+        if (games[i]->cv) {
+            cleanup();
+            return fail(ctx, PG_EUNSUPPORTED, "pg_solve_batch: games with repeated priorities are solved one at a time");
+        }
         nmax = std::max<int64_t>(nmax, games[i]->n);
     }
     pg_game* g = nullptr;

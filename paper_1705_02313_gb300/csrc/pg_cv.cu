@@ -1,0 +1,469 @@
+// Count-vector mode: valuations of games whose priorities repeat (Section 3,
+// "Valuations": L(p) counts how often priority p occurs on the play from v to
+// the sink, v included), for at most kMaxLevels distinct priorities.
+//
+// Ids are ranks by (priority, input order), so the ids of one priority form
+// a range (a level) and the largest id on a cycle has the cycle's largest
+// priority. A count vector is encoded as one signed 128-bit key
+//   key(v) = sum over levels l of s_l * L_l(v) * 2^(25 l),  s_l = +1 (even), -1 (odd),
+// whose digits stay below 2^24 in magnitude (fewer than 2^24 ids), so keys
+// compare exactly as valuations do under Maxdiff: the largest level whose
+// counts differ decides, more is better when its priority is even. The key is
+// a sum of per-vertex weights along the play, computed over the same
+// nearest-greater decomposition as the distinct-priority path:
+//   k_walk_cv      g(v) by a direct walk, with the weight of the segment [v, g(v))
+//   k_jump_cv_coop pointer jumping for the walks that ran out of steps, with
+//                  the weights (two buffers per round, so every read sees one
+//                  consistent (word, weight) pair)
+//   k_chain_cv     classification and key = sum of segment weights along the g-chain
+//   k_switch_cv    the switching rules of Section 3 and Section 4 on the keys
+#include "pg_internal.cuh"
+
+namespace pg {
+namespace {
+
+using i128 = __int128;
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kIlpCv = 4;
+
+__device__ inline i128 top_key() { return (i128)(~(unsigned __int128)0 >> 1); }
+
+__device__ inline int level_of(const Levels& L, int32_t v) {
+    int l = 0;
+    while (l + 1 < L.n && v >= L.start[l + 1]) ++l;
+    return l;
+}
+
+__device__ inline i128 weight_of(const Levels& L, int32_t v) {
+    const int l = level_of(L, v);
+    const i128 w = (i128)1 << (kDigitBits * l);
+    return ((L.odd_mask >> l) & 1u) ? -w : w;
+}
+
+inline unsigned grid_n(int64_t n) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+inline unsigned grid_ilp(int64_t n) {
+    int64_t tiles = (n + 32 * kIlpCv - 1) / (32 * kIlpCv);
+    int64_t b = (tiles + kBlock / 32 - 1) / (kBlock / 32);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+__device__ inline uint32_t g32_word(uint64_t w) {
+    return (gd_none(w) ? 0x80000000u : 0u) | (gd_sink(w) ? 0x40000000u : 0u) | (uint32_t)gd_ptr(w);
+}
+__device__ inline bool w32_none(uint32_t w) { return (w & 0x80000000u) != 0; }
+__device__ inline bool w32_sink(uint32_t w) { return (w & 0x40000000u) != 0; }
+__device__ inline int32_t w32_ptr(uint32_t w) { return (int32_t)(w & 0x3fffffffu); }
+
+__device__ inline void block_add32(int32_t v, int32_t* counter) {
+    __shared__ int32_t acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&acc, v);
+    __syncthreads();
+    if (threadIdx.x == 0 && acc) atomicAdd(counter, acc);
+}
+
+// Bounded software grid barrier (all blocks co-resident in a cooperative
+// launch); records kErrBarrier and returns false when it gives up.
+__device__ bool grid_sync_cv(Counters* c) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile uint32_t* genp = &c->bar_gen;
+        const uint32_t gen = *genp;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            int64_t spins = 0;
+            while (*genp == gen) {
+                if (++spins > (1ll << 24)) {
+                    atomicOr(&c->err, kErrBarrier);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Nearest greater vertex by a direct walk of at most kWalkCap steps, summing
+// the weights of the vertices passed (v included, g(v) not). Both buffers get
+// the result; walks that run out of steps join the pending list.
+__global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const int32_t* __restrict__ strat,
+                                                    const uint8_t* __restrict__ flags, int32_t sink0,
+                                                    uint64_t* __restrict__ gd, uint64_t* __restrict__ gdB,
+                                                    uint32_t* __restrict__ gd32, i128* __restrict__ ws,
+                                                    i128* __restrict__ wsB, int32_t* __restrict__ plist,
+                                                    Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 32 * kIlpCv < n;
+         tile += nwarps) {
+        int32_t v[kIlpCv], x[kIlpCv];
+        uint32_t d[kIlpCv];
+        i128 acc[kIlpCv];
+        bool act[kIlpCv], slotid[kIlpCv];
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            v[j] = (int32_t)(tile * 32 * kIlpCv + lane + 32 * j);
+            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
+            d[j] = 1;
+            acc[j] = (v[j] < n && !slotid[j]) ? weight_of(L, v[j]) : 0;
+            act[j] = v[j] < n && !slotid[j] && x[j] < v[j];
+        }
+        for (;;) {
+            bool any = false;
+            int32_t nx[kIlpCv];
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                if (act[j] && d[j] >= (uint32_t)kWalkCap) act[j] = false;  // pending at x (not summed)
+                nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                if (act[j]) {
+                    acc[j] += weight_of(L, x[j]);
+                    x[j] = nx[j];
+                    ++d[j];
+                    act[j] = x[j] < v[j];
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            bool pend = false;
+            if (v[j] < n) {
+                uint64_t w;
+                if (slotid[j]) w = gd_pack(true, false, 0, v[j], true);
+                else if (x[j] > v[j]) w = gd_pack(true, false, d[j], x[j], x[j] == sink0);
+                else if (x[j] == v[j]) w = gd_pack(true, true, d[j], v[j]);
+                else {
+                    w = gd_pack(false, false, d[j], x[j]);
+                    pend = true;
+                }
+                gd[v[j]] = w;
+                gdB[v[j]] = w;
+                gd32[v[j]] = g32_word(w);
+                ws[v[j]] = acc[j];
+                wsB[v[j]] = acc[j];
+            }
+            const unsigned m = __ballot_sync(kFullMask, pend);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int32_t base = 0;
+                if (lane == leader) base = atomicAdd(&cnt->n_pending, __popc(m));
+                base = __shfl_sync(kFullMask, base, leader);
+                if (pend) plist[base + __popc(m & ((1u << lane) - 1u))] = v[j];
+            }
+        }
+    }
+}
+
+// Pointer jumping with weights, all rounds in one cooperative launch. Round r
+// reads buffer r % 2 and writes the other for every pending-list vertex
+// (copying finished ones forward), so a vertex's word and weight are always
+// read from the same round. The final values end in the first buffer.
+__global__ void __launch_bounds__(kBlock) k_jump_cv_coop(const int32_t* __restrict__ plist, uint64_t* gd,
+                                                         uint64_t* gdB, i128* ws, i128* wsB, uint32_t* gd32,
+                                                         int32_t sink0, Counters* cnt, int32_t cap) {
+    const int32_t np = cnt->n_pending;
+    if (np == 0) return;
+    for (int32_t r = 0;; ++r) {
+        uint64_t* sg = (r & 1) ? gdB : gd;
+        uint64_t* dg = (r & 1) ? gd : gdB;
+        i128* sw = (r & 1) ? wsB : ws;
+        i128* dw = (r & 1) ? ws : wsB;
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt->left[(r + 1) % 3] = 0;
+        int32_t left = 0;
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+            const int32_t v = plist[i];
+            const uint64_t w = __ldcg((const unsigned long long*)(sg + v));
+            const i128 a = sw[v];
+            if (gd_resolved(w)) {
+                dg[v] = w;
+                dw[v] = a;
+                continue;
+            }
+            const int32_t x = gd_ptr(w);
+            const uint64_t wx = __ldcg((const unsigned long long*)(sg + x));
+            const i128 ax = sw[x];
+            uint64_t nw;
+            if (gd_resolved(wx) && gd_none(wx)) {
+                nw = gd_pack(true, true, 0, gd_ptr(wx));  // v is above its whole future, in a top basin
+            } else {
+                const int32_t y = gd_ptr(wx);
+                uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
+                if (nd > kDistMax) nd = kDistMax;
+                if (y > v) nw = gd_pack(true, false, (uint32_t)nd, y, y == sink0);
+                else if (y == v) nw = gd_pack(true, true, (uint32_t)nd, v);
+                else {
+                    nw = gd_pack(false, false, (uint32_t)nd, y);
+                    ++left;
+                }
+            }
+            dg[v] = nw;
+            dw[v] = a + ax;
+            if (gd_resolved(nw)) gd32[v] = g32_word(nw);
+        }
+        block_add32(left, &cnt->left[r % 3]);
+        if (!grid_sync_cv(cnt)) return;
+        const int32_t rem = *(volatile int32_t*)&cnt->left[r % 3];
+        if (rem == 0 || r + 1 >= cap) {
+            if (rem != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cnt->err, kErrJumpRounds);
+            if (blockIdx.x == 0 && threadIdx.x == 0) cnt->jump_rounds = r + 1;
+            if (!(r & 1)) {  // this round wrote the second buffer: bring the results back
+                for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+                    const int32_t v = plist[i];
+                    gd[v] = gdB[v];
+                    ws[v] = wsB[v];
+                }
+            }
+            return;
+        }
+    }
+}
+
+// Classification and keys: each vertex sums the segment weights along its
+// g-chain to the sink (finite) or meets a vertex above its whole future
+// (top; the cycle's largest priority is that vertex's maximum's).
+__global__ void __launch_bounds__(kBlock) k_chain_cv(int32_t n, const uint32_t* __restrict__ gd32,
+                                                     const i128* __restrict__ ws, const uint8_t* __restrict__ flags,
+                                                     const int32_t* __restrict__ pri, i128* __restrict__ key,
+                                                     uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
+                                                     int32_t* __restrict__ dom, int want_dom, GameState* gst,
+                                                     Counters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int32_t nfin = 0, nodd = 0;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 32 * kIlpCv < n;
+         tile += nwarps) {
+        int32_t v[kIlpCv], x[kIlpCv], cyc[kIlpCv];
+        i128 acc[kIlpCv];
+        bool act[kIlpCv], slotid[kIlpCv];
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            v[j] = (int32_t)(tile * 32 * kIlpCv + lane + 32 * j);
+            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            const uint32_t w = (v[j] < n && !slotid[j]) ? gd32[v[j]] : 0x40000000u;
+            cyc[j] = w32_none(w) ? w32_ptr(w) : -1;
+            acc[j] = (v[j] < n && !slotid[j] && cyc[j] < 0) ? ws[v[j]] : 0;
+            x[j] = w32_ptr(w);
+            act[j] = v[j] < n && !slotid[j] && !w32_none(w) && !w32_sink(w);
+        }
+        for (;;) {
+            bool any = false;
+            uint32_t wx[kIlpCv];
+            i128 ax[kIlpCv];
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                wx[j] = act[j] ? gd32[x[j]] : 0u;
+                ax[j] = act[j] ? ws[x[j]] : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                if (act[j]) {
+                    if (w32_none(wx[j])) {
+                        cyc[j] = w32_ptr(wx[j]);
+                        act[j] = false;
+                    } else {
+                        acc[j] += ax[j];
+                        x[j] = w32_ptr(wx[j]);
+                        act[j] = !w32_sink(wx[j]);
+                    }
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            if (v[j] >= n) continue;
+            if (slotid[j]) {
+                key[v[j]] = 0;  // the sink: the empty valuation
+                kind[v[j]] = 8;
+                cls[v[j]] = kFin;
+                if (want_dom) dom[v[j]] = -1;
+            } else if (cyc[j] < 0) {
+                key[v[j]] = acc[j];
+                kind[v[j]] = 1;  // finite (read by the depth pass)
+                cls[v[j]] = kFin;
+                if (want_dom) dom[v[j]] = -1;
+                ++nfin;
+            } else {
+                const bool odd = (flags[cyc[j]] & kPriOdd) != 0;
+                key[v[j]] = top_key();
+                kind[v[j]] = 0;
+                cls[v[j]] = odd ? kOddCycle : kTop;
+                if (want_dom) dom[v[j]] = pri[cyc[j]];
+                if (odd) {
+                    ++nodd;
+                    atomicAdd(&gst[0].nodd, 1);
+                }
+            }
+        }
+    }
+    block_add32(nfin, &cnt->n_fin);
+    block_add32(nodd, &cnt->n_odd);
+}
+
+// The switching rules on keys (first minimiser for Odd; the sink first, then
+// the first maximiser for Even; strictly better only), one thread per vertex.
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_switch_cv(int32_t n, int player, const OffT* __restrict__ off,
+                                                      const int32_t* __restrict__ tgt,
+                                                      const uint8_t* __restrict__ flags, const i128* __restrict__ key,
+                                                      int32_t sink0, GameState* gst, int32_t* strat, Counters* cnt) {
+    {
+        const GameState st = gst[0];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
+    }
+    int32_t nsw = 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        if ((f & kSinkSlot) || (int)(f & kOwnerOdd) != player) continue;
+        const int64_t e0 = off[v], e1 = off[v + 1];
+        const int32_t cur = strat[v];
+        int32_t best = player == 0 ? sink0 : -1;
+        i128 bk = player == 0 ? key[sink0] : 0;
+        const i128 curkey = key[cur];
+        for (int64_t e = e0; e < e1; e += 4) {
+            int32_t t[4];
+            i128 kk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? tgt[e + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kk[j] = t[j] >= 0 ? key[t[j]] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (t[j] < 0) continue;
+                const bool better = player == 0 ? kk[j] > bk : (best < 0 || kk[j] < bk);
+                if (better) {
+                    best = t[j];
+                    bk = kk[j];
+                }
+            }
+        }
+        if (player == 0 ? bk > curkey : bk < curkey) {
+            strat[v] = best;
+            ++nsw;
+        }
+    }
+    block_add32(nsw, &cnt->n_switch);
+    __shared__ int32_t tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int32_t x = nsw;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&tot, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && tot) atomicAdd(player ? &gst[0].sw_odd : &gst[0].sw_even, tot);
+}
+
+// Count vectors of the original vertices (rows of nlev), decoded from the
+// keys: balanced base-2^25 digits, each the signed count of its level.
+__global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i128* __restrict__ key,
+                         const uint8_t* __restrict__ cls, Levels L, int32_t* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = nid0[v];
+        const bool fin = cls[i] == kFin;
+        i128 k = fin ? key[i] : 0;
+        for (int l = 0; l < L.n; ++l) {
+            // the lowest digit in (-2^24, 2^24): low 25 bits, taken negative from 2^24 up
+            int64_t a = (int64_t)(k & (i128)((1 << kDigitBits) - 1));
+            if (a >= (1ll << (kDigitBits - 1))) a -= 1ll << kDigitBits;
+            k = (k - (i128)a) >> kDigitBits;  // exact: k - a is a multiple of 2^25
+            out[v * L.n + l] = (int32_t)(((L.odd_mask >> l) & 1u) ? -a : a);
+        }
+    }
+}
+
+}  // namespace
+
+pg_status alloc_cv(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    const int64_t n = g->n;
+    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->ws, sizeof(i128) * n));
+    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->wsB, sizeof(i128) * n));
+    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->gdB, sizeof(uint64_t) * n));
+    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->key128, sizeof(i128) * n));
+    return PG_OK;
+}
+
+pg_status enqueue_valuation_cv(pg_game* g, bool want_dom) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int32_t n = g->n;
+    Counters* c = g->cnt;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
+    prof_begin(g, KID_WALK);
+    k_walk_cv<<<grid_ilp(n), kBlock, 0, s>>>(n, g->lev, g->strat, g->flags, g->sink0, g->gd, g->gdB, g->gd32, g->ws,
+                                             g->wsB, g->plist, c);
+    prof_end(g, KID_WALK, 1);
+    {
+        int32_t cap = 64;
+        for (int64_t x = n; x > 1; x >>= 1) cap += 2;
+        void* args[] = {(void*)&g->plist, (void*)&g->gd,    (void*)&g->gdB, (void*)&g->ws, (void*)&g->wsB,
+                        (void*)&g->gd32,  (void*)&g->sink0, (void*)&c,      (void*)&cap};
+        prof_begin(g, KID_JUMP);
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_cv_coop, g->coop_blocks, kBlock, args, 0, s));
+        prof_end(g, KID_JUMP, 1);
+    }
+    prof_begin(g, KID_CHAIN2);
+    k_chain_cv<<<grid_ilp(n), kBlock, 0, s>>>(n, g->gd32, g->ws, g->flags, g->pri, g->key128, g->kind, g->cls,
+                                              g->dom, want_dom ? 1 : 0, g->gst, c);
+    prof_end(g, KID_CHAIN2, 1);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_switch_cv(pg_game* g, int player) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
+    const int kid = player ? KID_SWITCH_ODD : KID_SWITCH_EVEN;
+    prof_begin(g, kid);
+    k_switch_cv<int32_t><<<grid_n(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->key128, g->sink0,
+                                                        g->gst, g->strat, g->cnt);
+    prof_end(g, kid, 1);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status write_counts(pg_game* g, int32_t mem_kind, int32_t* counts) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = sizeof(int32_t) * (size_t)g->n0 * (size_t)g->lev.n;
+    int32_t* dst = counts;
+    if (mem_kind == PG_MEM_HOST) PG_CUDA_TRY(ctx, cudaMallocAsync((void**)&dst, bytes ? bytes : 4, s));
+    ctx->launches += 1;
+    k_counts<<<grid_n(g->n0), kBlock, 0, s>>>(g->n0, g->nid0, g->key128, g->cls, g->lev, dst);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem_kind == PG_MEM_HOST)
+        e = cudaMemcpyAsync(counts, dst, bytes, cudaMemcpyDeviceToHost, s);
+    if (mem_kind == PG_MEM_HOST) cudaFreeAsync(dst, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "write_counts");
+    return PG_OK;
+}
+
+}  // namespace pg

@@ -23,6 +23,13 @@ constexpr int kBlock = 256;
 constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
 constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
+// Count-vector mode (repeated priorities): at most kMaxLevels distinct
+// priorities; a count vector is one signed 128-bit key with one base-2^25
+// digit per level (fewer than 2^24 ids, so every digit stays below 2^24 in
+// magnitude and the key order is the order of Section 3).
+constexpr int kMaxLevels = 5;
+constexpr int kDigitBits = 25;
+constexpr int32_t kMaxCvIds = (1 << 24) - 1;
 
 // flags[v]
 constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
@@ -133,6 +140,14 @@ struct GameState {
 constexpr int32_t kPhaseActive = 0, kPhaseDone = 1, kPhaseOddCycle = 2, kPhaseTimeout = 3;
 }  // namespace pg
 
+// Levels of a count-vector game: ids [start[l], start[l+1]) have the l-th
+// smallest priority; bit l of odd_mask is that priority's parity.
+struct Levels {
+    int32_t n;
+    uint32_t odd_mask;
+    int32_t start[pg::kMaxLevels + 1];
+};
+
 // A loaded game, or a batch of games packed into one id space. Every game's
 // relabelled G' vertices occupy a contiguous id range followed by one "sink
 // slot" id that stands for that game's sink (greater than every vertex of the
@@ -146,6 +161,14 @@ struct pg_game {
     int32_t n = 0;    // ids: G' vertices of all games plus one sink slot per game
     int64_t m = 0;    // edges of all G'
     int32_t sink0 = 0;           // the sink slot of game 0 (the only one for a single game)
+    // count-vector mode (repeated priorities; single games only)
+    bool cv = false;
+    Levels lev{};
+    int32_t lev_pri[pg::kMaxLevels] = {};  // the G' priority of each level
+    __int128* ws = nullptr;      // [n] key weight of the walk segment [v, g(v))
+    __int128* wsB = nullptr;     // [n] second buffer of the pointer-jumping rounds
+    uint64_t* gdB = nullptr;     // [n] second buffer of the nearest-greater words
+    __int128* key128 = nullptr;  // [n] count-vector key; a sink slot holds 0
     // packed relabelled G'
     int32_t* off = nullptr;      // [n+1] int32 edge offsets (when m < 2^31), else off64
     int64_t* off64 = nullptr;    // [n+1]
@@ -277,6 +300,11 @@ pg_status enqueue_depth(pg_game* g);
 pg_status enqueue_switch(pg_game* g, int player);
 // Copies the counters to g->hcnt and waits for the stream; checks device error bits.
 pg_status sync_counters(pg_game* g);
+// Count-vector mode (pg_cv.cu): scratch, one valuation, one switching pass, counts output.
+pg_status alloc_cv(pg_game* g);
+pg_status enqueue_valuation_cv(pg_game* g, bool want_dom);
+pg_status enqueue_switch_cv(pg_game* g, int player);
+pg_status write_counts(pg_game* g, int32_t mem_kind, int32_t* counts);
 }  // namespace pg
 
 #define PG_CUDA_TRY(ctx, expr)                                    \

@@ -1098,6 +1098,10 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A(&g->scan_tmp, g->scan_tmp_bytes));
     pg_status st = coop_blocks_for(ctx, &g->coop_blocks);
     if (st) return st;
+    if (g->cv) {
+        pg_status st2 = alloc_cv(g);
+        if (st2) return st2;
+    }
     for (int i = 0; i < 4; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->ev[i]));
     for (int i = 0; i < 2 * KID_COUNT; ++i) PG_CUDA_TRY(ctx, cudaEventCreate(&g->kev[i]));
     return reset_scratch(g);
@@ -1129,6 +1133,7 @@ pg_status reset_games(pg_game* g) {
 }
 
 pg_status enqueue_valuation(pg_game* g, bool want_dom) {
+    if (g->cv) return enqueue_valuation_cv(g, want_dom);
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     int32_t n = g->n;
@@ -1191,6 +1196,7 @@ pg_status enqueue_depth(pg_game* g) {
 }
 
 pg_status enqueue_switch(pg_game* g, int player) {
+    if (g->cv) return enqueue_switch_cv(g, player);
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));

@@ -48,10 +48,10 @@ __global__ void k_validate(int32_t n, int64_t m, const int32_t* off, const int32
 
 // Marks every priority in a bitmap; a bit already set means a repeated priority.
 __global__ void k_mark_priorities(int32_t n, const int32_t* pri, int32_t shift_orig, int32_t n_orig,
-                                  uint32_t* bits, LoadScalars* sc) {
+                                  uint32_t* bits, LoadScalars* sc, int dummy_zero) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        // vertices below n_orig are original (priority shifted by shift_orig); the rest are dummies with 2j
-        int64_t p = v < n_orig ? (int64_t)pri[v] + shift_orig : 2 * (v - n_orig);
+        // vertices below n_orig are original (priority shifted by shift_orig); the rest are dummies with 2j (0)
+        int64_t p = v < n_orig ? (int64_t)pri[v] + shift_orig : (dummy_zero ? 0 : 2 * (v - n_orig));
         uint32_t bit = 1u << (p & 31);
         uint32_t old = atomicOr(&bits[p >> 5], bit);
         if (old & bit) atomicOr(&sc->err, kEDup);
@@ -115,7 +115,10 @@ __global__ void k_dummy_of(int32_t n, const uint8_t* isW, const int32_t* widx, i
         if (isW[w]) dummy_of[widx[w]] = (int32_t)w;
 }
 
-__device__ inline int32_t prio_of(int64_t v, int32_t n0, const int32_t* pri, int32_t k) {
+// G' priority: distinct priorities (cv = 0): originals + 2k, dummy j has 2j;
+// repeated priorities (cv = 1): originals + 2, every dummy 0.
+__device__ inline int32_t prio_of(int64_t v, int32_t n0, const int32_t* pri, int32_t k, int cv) {
+    if (cv) return v < n0 ? pri[v] + 2 : 0;
     return v < n0 ? pri[v] + 2 * k : (int32_t)(2 * (v - n0));
 }
 
@@ -123,8 +126,34 @@ __device__ inline int32_t prio_of(int64_t v, int32_t n0, const int32_t* pri, int
 __global__ void k_rank(int32_t np, int32_t n0, int32_t k, const int32_t* pri, const uint32_t* bits,
                        const int32_t* wprefix, int32_t* nid, int32_t* gid) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < np; v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t p = prio_of(v, n0, pri, k);
+        int32_t p = prio_of(v, n0, pri, k, 0);
         int32_t r = wprefix[p >> 5] + __popc(bits[p >> 5] & ((1u << (p & 31)) - 1u));
+        nid[v] = r;
+        gid[r] = (int32_t)v;
+    }
+}
+
+// Repeated priorities: level of every G' vertex = rank of its priority value
+// among the distinct values.
+__global__ void k_level(int32_t np, int32_t n0, const int32_t* pri, const uint32_t* bits, const int32_t* wprefix,
+                        uint8_t* lvl) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < np; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p = prio_of(v, n0, pri, 0, 1);
+        lvl[v] = (uint8_t)(wprefix[p >> 5] + __popc(bits[p >> 5] & ((1u << (p & 31)) - 1u)));
+    }
+}
+
+__global__ void k_is_level(int32_t np, const uint8_t* lvl, int32_t l, uint8_t* ind) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < np; v += (int64_t)gridDim.x * blockDim.x)
+        ind[v] = lvl[v] == l;
+}
+
+// relabelled id = first id of the level + position among the level's vertices in G' order
+__global__ void k_assign_level(int32_t np, const uint8_t* lvl, int32_t l, int32_t start, const int32_t* pos,
+                               int32_t* nid, int32_t* gid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < np; v += (int64_t)gridDim.x * blockDim.x) {
+        if (lvl[v] != l) continue;
+        const int32_t r = start + pos[v];
         nid[v] = r;
         gid[r] = (int32_t)v;
     }
@@ -141,10 +170,10 @@ __global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int32_t*
                                const uint8_t* own, const int32_t* pri, const uint8_t* inU, const int32_t* widx,
                                const int32_t* dummy_of, const int32_t* gid, const int32_t* nid,
                                const int32_t* roff, int32_t* rtgt, uint8_t* rflags, int32_t* rpri,
-                               int32_t* orig_of) {
+                               int32_t* orig_of, int cv) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t src = gid[i];
-        int32_t p = prio_of(src, n0, pri, k);
+        int32_t p = prio_of(src, n0, pri, k, cv);
         int32_t base = roff[i];
         if (src < n0) {
             bool u = inU[src] != 0;
@@ -237,18 +266,18 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     if (h.err & kEPri) return fail(ctx, PG_EINVAL, "pg_load_csr: negative priority");
     int32_t maxpri = h.maxpri;
 
-    // repeated priorities are outside this version
+    // repeated priorities select the count-vector mode
+    bool cv = false;
     {
         int64_t nwords = ((int64_t)maxpri >> 5) + 1;
         uint32_t* bits;
         PG_CUDA_TRY(ctx, T.get(&bits, nwords));
         PG_CUDA_TRY(ctx, cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)nwords, s));
         ++ctx->launches;
-        k_mark_priorities<<<nblocks(n), kBlock, 0, s>>>(n, pri, 0, n, bits, sc);
+        k_mark_priorities<<<nblocks(n), kBlock, 0, s>>>(n, pri, 0, n, bits, sc, 0);
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
         PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        if (h.err & kEDup)
-            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities are not supported by this version");
+        cv = (h.err & kEDup) != 0;
     }
 
     // reverse adjacency for the trap computation
@@ -303,8 +332,10 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     int64_t np = (int64_t)n + k, mp = m + k;
     if (np >= (1 << 29) - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^29 vertices after preprocessing");
     if (mp > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^31-2 edges after preprocessing");
-    if ((int64_t)maxpri + 2 * (int64_t)k > INT32_MAX - 1)
+    if ((int64_t)maxpri + (cv ? 2 : 2 * (int64_t)k) > INT32_MAX - 1)
         return fail(ctx, PG_EINVAL, "pg_load_csr: priorities too large for the preprocessing shift");
+    if (cv && np + 1 > kMaxCvIds)
+        return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities need fewer than 2^24 vertices after preprocessing");
 
     pg_game* g = new pg_game();
     g->ctx = ctx;
@@ -340,7 +371,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
 
     // ranks of the G' priorities
-    int64_t pmax = (int64_t)maxpri + 2 * (int64_t)k;
+    int64_t pmax = (int64_t)maxpri + (cv ? 2 : 2 * (int64_t)k);
     int64_t nw = (pmax >> 5) + 1;
     uint32_t* bits2;
     int32_t *wprefix, *nid, *gid, *deg;
@@ -355,18 +386,52 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     LG_TRY(cudaMemsetAsync(bits2, 0, sizeof(uint32_t) * (size_t)nw, s));
     LG_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int32_t), s));
     ++ctx->launches;
-    k_mark_priorities<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, pri, 2 * k, n, bits2, sc);
+    k_mark_priorities<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, pri, cv ? 2 : 2 * k, n, bits2, sc, cv ? 1 : 0);
     ctx->launches += 3;
     LG_TRY(exclusive_popc_scan(bits2, wprefix, nw, stmp2, stb2, s));
-    ++ctx->launches;
-    k_rank<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, pri, bits2, wprefix, nid, gid);
+    if (!cv) {
+        ++ctx->launches;
+        k_rank<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, pri, bits2, wprefix, nid, gid);
+    } else {
+        // levels: the distinct priorities of G'; ids by (priority, G' order)
+        int32_t nlev = 0;
+        LG_TRY(cudaMemcpyAsync(&nlev, wprefix + nw, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LG_TRY(cudaStreamSynchronize(s));
+        if (nlev > kMaxLevels) {
+            free_game(g);
+            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities support at most 5 distinct priorities "
+                                              "after preprocessing (the dummies' priority counts as one)");
+        }
+        uint8_t *lvl8, *ind;
+        int32_t* pos;
+        LG_TRY(T.get(&lvl8, np));
+        LG_TRY(T.get(&ind, np));
+        LG_TRY(T.get(&pos, np + 1));
+        ++ctx->launches;
+        k_level<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, pri, bits2, wprefix, lvl8);
+        g->cv = true;
+        g->lev.n = nlev;
+        int32_t start = 0;
+        for (int32_t l = 0; l < nlev; ++l) {
+            g->lev.start[l] = start;
+            ctx->launches += 5;
+            k_is_level<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, lvl8, l, ind);
+            LG_TRY(exclusive_scan_u8(ind, pos, np, stmp2, stb2, s));
+            k_assign_level<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, lvl8, l, start, pos, nid, gid);
+            int32_t cnt_l = 0;
+            LG_TRY(cudaMemcpyAsync(&cnt_l, pos + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LG_TRY(cudaStreamSynchronize(s));
+            start += cnt_l;
+        }
+        g->lev.start[nlev] = start;
+    }
     ++ctx->launches;
     k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);
     ctx->launches += 3;
     LG_TRY(exclusive_scan_i32(deg, g->off, np, nullptr, stmp2, stb2, s));
     ++ctx->launches;
     k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, widx, g->dummy_of,
-                                                  gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of);
+                                                  gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of, cv ? 1 : 0);
     ++ctx->launches;
     k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
     // the sink slot: no edges, a flag, no priority or original vertex
@@ -383,7 +448,14 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     LG_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
     LG_TRY(cudaStreamSynchronize(s));
     LG_TRY(cudaGetLastError());
-    if (h.err & kEDup) {
+    if (cv) {  // each level's priority and parity
+        g->lev.odd_mask = 0;
+        for (int32_t l = 0; l < g->lev.n; ++l) {
+            LG_TRY(cudaMemcpy(&g->lev_pri[l], g->pri + g->lev.start[l], sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (g->lev_pri[l] & 1) g->lev.odd_mask |= 1u << l;
+        }
+    }
+    if (!cv && (h.err & kEDup)) {
         free_game(g);
         return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: internal priority collision after preprocessing");
     }

@@ -324,6 +324,10 @@ void loader_main(pg_server* sv) {
         pg_game* gi = nullptr;
         pg_status st = load_game(ctx, p.n, p.m, p.off.data(), p.tgt.data(), p.own.data(), p.pri.data(), PG_MEM_HOST,
                                  &gi, false);
+        if (st == PG_OK && gi->cv) {  // the packed batch ranks distinct priorities only
+            free_game(gi);
+            st = PG_EUNSUPPORTED;
+        }
         if (st != PG_OK) {
             if (st == PG_ECUDA) {
                 set_fatal(sv, st, ctx);

@@ -37,7 +37,7 @@ class PgError(RuntimeError):
 class pg_result(C.Structure):
     _fields_ = [("win", C.c_void_p), ("sigma", C.c_void_p), ("tau", C.c_void_p), ("val_class", C.c_void_p),
                 ("val_depth", C.c_void_p), ("val_rank", C.c_void_p), ("dummy_sigma", C.c_void_p),
-                ("mem_kind", C.c_int32), ("major", C.c_int64), ("inner", C.c_int64)]
+                ("mem_kind", C.c_int32), ("major", C.c_int64), ("inner", C.c_int64), ("val_counts", C.c_void_p)]
 
 
 class pg_solve_opts(C.Structure):
@@ -47,7 +47,7 @@ class pg_solve_opts(C.Structure):
 
 class pg_valuation(C.Structure):
     _fields_ = [("val_class", C.c_void_p), ("val_depth", C.c_void_p), ("val_rank", C.c_void_p),
-                ("dom", C.c_void_p), ("mem_kind", C.c_int32)]
+                ("dom", C.c_void_p), ("mem_kind", C.c_int32), ("val_counts", C.c_void_p)]
 
 
 class pg_result_batch(C.Structure):
@@ -104,6 +104,7 @@ def lib():
     L.pg_game_free.restype = None
     L.pg_game_info.argtypes = [P, C.POINTER(I32), C.POINTER(I64), C.POINTER(I32)]
     L.pg_game_dummies.argtypes = [P, P]
+    L.pg_game_levels.argtypes = [P, C.POINTER(I32), P]
     L.pg_solve.argtypes = [P, C.POINTER(pg_solve_opts), C.POINTER(pg_result)]
     L.pg_best_response.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
     L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
@@ -128,7 +129,7 @@ def lib():
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop", "pg_server_create", "pg_server_submit", "pg_server_poll",
-                 "pg_server_fetch", "pg_server_get_stats"]:
+                 "pg_server_fetch", "pg_server_get_stats", "pg_game_levels"]:
         getattr(L, name).restype = I32
     _lib = L
     return L
@@ -230,6 +231,17 @@ def pg_game_info(game):
     return n.value, m.value, k.value
 
 
+def pg_game_levels(game):
+    """Count-vector mode: the distinct priorities of G' in ascending order
+    (an empty array for a game with distinct priorities)."""
+    d = C.c_int32(0)
+    lp = np.zeros(8, np.int32)
+    rc = lib().pg_game_levels(game, C.byref(d), lp.ctypes.data)
+    if rc != PG_OK:
+        raise PgError(rc, "pg_game_levels")
+    return lp[: d.value].copy()
+
+
 def pg_game_dummies(game):
     n, m, k = pg_game_info(game)
     out = np.zeros(max(k, 1), np.int32)
@@ -240,17 +252,21 @@ def pg_game_dummies(game):
 
 
 def pg_solve(ctx, game, win=None, sigma=None, tau=None, val_class=None, val_depth=None, val_rank=None,
-             dummy_sigma=None, sigma_init=None, tau_init=None, dummy_sigma_init=None, max_inner=0, reset_tau=False):
+             dummy_sigma=None, sigma_init=None, tau_init=None, dummy_sigma_init=None, max_inner=0, reset_tau=False,
+             val_counts=None):
     """Fills the given output arrays (all in host memory or all in device
-    memory); returns (major, inner)."""
+    memory); returns (major, inner). val_counts (n x d int32) is filled in
+    count-vector mode (games whose priorities repeat)."""
     _dtype_check(win, np.uint8, "win")
-    for a, nm in [(sigma, "sigma"), (tau, "tau"), (val_depth, "val_depth"), (val_rank, "val_rank")]:
+    for a, nm in [(sigma, "sigma"), (tau, "tau"), (val_depth, "val_depth"), (val_rank, "val_rank"),
+                  (val_counts, "val_counts")]:
         _dtype_check(a, np.int32, nm)
     _dtype_check(val_class, np.int8, "val_class")
     _dtype_check(dummy_sigma, np.int8, "dummy_sigma")
     res = pg_result(_ptr_kind(win)[0], _ptr_kind(sigma)[0], _ptr_kind(tau)[0], _ptr_kind(val_class)[0],
                     _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dummy_sigma)[0],
-                    _same_kind(win, sigma, tau, val_class, val_depth, val_rank, dummy_sigma), 0, 0)
+                    _same_kind(win, sigma, tau, val_class, val_depth, val_rank, dummy_sigma, val_counts), 0, 0,
+                    _ptr_kind(val_counts)[0])
     opts = pg_solve_opts(_ptr_kind(sigma_init)[0], _ptr_kind(tau_init)[0], _ptr_kind(dummy_sigma_init)[0],
                          _same_kind(sigma_init, tau_init, dummy_sigma_init), int(max_inner), 1 if reset_tau else 0)
     rc = lib().pg_solve(game, C.byref(opts), C.byref(res))
@@ -259,11 +275,11 @@ def pg_solve(ctx, game, win=None, sigma=None, tau=None, val_class=None, val_dept
 
 
 def pg_best_response(ctx, game, sigma, tau_inout=None, dummy_sigma=None, val_class=None, val_depth=None,
-                     val_rank=None, dom=None):
+                     val_rank=None, dom=None, val_counts=None):
     _dtype_check(sigma, np.int32, "sigma")
     _dtype_check(tau_inout, np.int32, "tau_inout")
     val = pg_valuation(_ptr_kind(val_class)[0], _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dom)[0],
-                       _same_kind(val_class, val_depth, val_rank, dom))
+                       _same_kind(val_class, val_depth, val_rank, dom, val_counts), _ptr_kind(val_counts)[0])
     iters = C.c_int64(0)
     rc = lib().pg_best_response(game, _ptr_kind(sigma)[0], _ptr_kind(dummy_sigma)[0], _ptr_kind(tau_inout)[0],
                                 _same_kind(sigma, tau_inout, dummy_sigma), C.byref(val), C.byref(iters))
@@ -272,10 +288,10 @@ def pg_best_response(ctx, game, sigma, tau_inout=None, dummy_sigma=None, val_cla
 
 
 def pg_valuate(ctx, game, sigma=None, tau=None, dummy_sigma=None, val_class=None, val_depth=None, val_rank=None,
-               dom=None):
+               dom=None, val_counts=None):
     """Returns the status code (PG_OK or PG_ENOTADMISSIBLE; outputs are filled in both cases)."""
     val = pg_valuation(_ptr_kind(val_class)[0], _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dom)[0],
-                       _same_kind(val_class, val_depth, val_rank, dom))
+                       _same_kind(val_class, val_depth, val_rank, dom, val_counts), _ptr_kind(val_counts)[0])
     rc = lib().pg_valuate(game, _ptr_kind(sigma)[0], _ptr_kind(dummy_sigma)[0], _ptr_kind(tau)[0],
                           _same_kind(sigma, tau, dummy_sigma), C.byref(val))
     if rc not in (PG_OK, PG_ENOTADMISSIBLE):

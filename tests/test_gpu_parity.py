@@ -253,8 +253,8 @@ def test_errors(pg, ctx):
     with pytest.raises(pg.PgError) as e:
         pg.pg_load_csr(ctx, ok.n, ok.m, ok.offsets, ok.targets, ok.owner, pri)
     assert e.value.code == pg.PG_EINVAL
-    pri = ok.pri.copy()
-    pri[1] = pri[0]
+    # repeated priorities: count-vector mode, at most 5 distinct priorities after preprocessing
+    pri = ok.pri % 7
     with pytest.raises(pg.PgError) as e:
         pg.pg_load_csr(ctx, ok.n, ok.m, ok.offsets, ok.targets, ok.owner, pri)
     assert e.value.code == pg.PG_EUNSUPPORTED
