@@ -142,6 +142,16 @@ void pg_game_free(pg_game *game);
 pg_status pg_game_info(const pg_game *game, int32_t *n, int64_t *m, int32_t *k);
 
 /* The vertex each dummy guards: out[j] = w for dummy j (k entries, host memory). */
+/* Counters of the last valuation on game (instrumentation): walks that ran
+ * out of direct steps and were finished by pointer jumping, the jumping
+ * rounds, finite vertices, vertices reaching an odd cycle, parents ranked
+ * by one block, parents ranked by the id-ordered scan, and the switches of
+ * the last switching pass. */
+typedef struct {
+    int32_t n_pending, jump_rounds, n_fin, n_odd, n_big, n_huge, n_switch;
+} pg_counters;
+pg_status pg_game_counters(const pg_game *game, pg_counters *out);
+
 /* Count-vector mode: *d receives the number of distinct priorities of G'
  * (0 for a game with distinct priorities) and level_pri (nullable, d <= 5
  * entries) their values in G' (original priority + 2; 0 for the dummies), in

@@ -518,6 +518,13 @@ pg_status pg_game_info(const pg_game* g, int32_t* n, int64_t* m, int32_t* k) {
     return PG_OK;
 }
 
+pg_status pg_game_counters(const pg_game* g, pg_counters* out) {
+    if (!g || !out || !g->hcnt) return PG_EINVAL;
+    const Counters& c = *g->hcnt;  // copied to the host at the end of every valuation
+    *out = {c.n_pending, c.jump_rounds, c.n_fin, c.n_odd, c.n_big, c.n_huge, c.n_switch};
+    return PG_OK;
+}
+
 pg_status pg_game_levels(const pg_game* g, int32_t* d, int32_t* level_pri) {
     if (!g || !d) return PG_EINVAL;
     *d = g->cv ? g->lev.n : 0;

@@ -102,14 +102,24 @@ __device__ bool grid_sync_cv(Counters* c) {
     return ok != 0;
 }
 
-// Nearest greater vertex by a direct walk of at most kWalkCap steps, summing
-// the weights of the vertices passed (v included, g(v) not). Both buffers get
-// the result; walks that run out of steps join the pending list.
+// Nearest greater vertex by a direct walk, summing the weights of the
+// vertices passed (v included, g(v) not). Both buffers get the result. As in
+// the distinct-priority walk, the first pass takes at most kWalkShort steps
+// and the walks still below their start continue densely in k_walk_more_cv
+// up to kWalkCap steps; those still pending join the pointer-jumping list.
+__device__ inline uint64_t cv_word(int32_t v, int32_t x, uint32_t d, int32_t sink0, bool* pend) {
+    *pend = false;
+    if (x > v) return gd_pack(true, false, d, x, x == sink0);
+    if (x == v) return gd_pack(true, true, d, v);
+    *pend = true;
+    return gd_pack(false, false, d, x);
+}
+
 __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const int32_t* __restrict__ strat,
                                                     const uint8_t* __restrict__ flags, int32_t sink0,
                                                     uint64_t* __restrict__ gd, uint64_t* __restrict__ gdB,
                                                     uint32_t* __restrict__ gd32, i128* __restrict__ ws,
-                                                    i128* __restrict__ wsB, int32_t* __restrict__ plist,
+                                                    i128* __restrict__ wsB, int32_t* __restrict__ more,
                                                     Counters* cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -133,7 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
             int32_t nx[kIlpCv];
 #pragma unroll
             for (int j = 0; j < kIlpCv; ++j) {
-                if (act[j] && d[j] >= (uint32_t)kWalkCap) act[j] = false;  // pending at x (not summed)
+                if (act[j] && d[j] >= (uint32_t)kWalkShort) act[j] = false;  // pending at x (not summed)
                 nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
             }
 #pragma unroll
@@ -152,14 +162,77 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
         for (int j = 0; j < kIlpCv; ++j) {
             bool pend = false;
             if (v[j] < n) {
-                uint64_t w;
-                if (slotid[j]) w = gd_pack(true, false, 0, v[j], true);
-                else if (x[j] > v[j]) w = gd_pack(true, false, d[j], x[j], x[j] == sink0);
-                else if (x[j] == v[j]) w = gd_pack(true, true, d[j], v[j]);
-                else {
-                    w = gd_pack(false, false, d[j], x[j]);
-                    pend = true;
+                const uint64_t w = slotid[j] ? gd_pack(true, false, 0, v[j], true) : cv_word(v[j], x[j], d[j], sink0, &pend);
+                gd[v[j]] = w;
+                gdB[v[j]] = w;
+                gd32[v[j]] = g32_word(w);
+                ws[v[j]] = acc[j];
+                wsB[v[j]] = acc[j];
+            }
+            const unsigned m = __ballot_sync(kFullMask, pend);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int32_t base = 0;
+                if (lane == leader) base = atomicAdd(&cnt->n_walk2, __popc(m));
+                base = __shfl_sync(kFullMask, base, leader);
+                if (pend) more[base + __popc(m & ((1u << lane) - 1u))] = v[j];
+            }
+        }
+    }
+}
+
+// Second walk pass over the list left by k_walk_cv, kIlpCv walks per thread.
+__global__ void __launch_bounds__(kBlock) k_walk_more_cv(Levels L, const int32_t* __restrict__ more,
+                                                         const int32_t* __restrict__ strat, int32_t sink0,
+                                                         uint64_t* __restrict__ gd, uint64_t* __restrict__ gdB,
+                                                         uint32_t* __restrict__ gd32, i128* __restrict__ ws,
+                                                         i128* __restrict__ wsB, int32_t* __restrict__ plist,
+                                                         Counters* cnt) {
+    const int32_t cntm = cnt->n_walk2;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 32 * kIlpCv < cntm;
+         tile += nwarps) {
+        int32_t v[kIlpCv], x[kIlpCv];
+        uint32_t d[kIlpCv];
+        i128 acc[kIlpCv];
+        bool act[kIlpCv], in[kIlpCv];
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            const int64_t i = tile * 32 * kIlpCv + lane + 32 * j;
+            in[j] = i < cntm;
+            v[j] = in[j] ? more[i] : 0;
+            const uint64_t w = in[j] ? gd[v[j]] : 0;
+            x[j] = gd_ptr(w);
+            d[j] = gd_dist(w);
+            acc[j] = in[j] ? ws[v[j]] : 0;
+            act[j] = in[j] && x[j] < v[j];
+        }
+        for (;;) {
+            bool any = false;
+            int32_t nx[kIlpCv];
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                if (act[j] && d[j] >= (uint32_t)kWalkCap) act[j] = false;
+                nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kIlpCv; ++j) {
+                if (act[j]) {
+                    acc[j] += weight_of(L, x[j]);
+                    x[j] = nx[j];
+                    ++d[j];
+                    act[j] = x[j] < v[j];
                 }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlpCv; ++j) {
+            bool pend = false;
+            if (in[j]) {
+                const uint64_t w = cv_word(v[j], x[j], d[j], sink0, &pend);
                 gd[v[j]] = w;
                 gdB[v[j]] = w;
                 gd32[v[j]] = g32_word(w);
@@ -417,8 +490,10 @@ pg_status enqueue_valuation_cv(pg_game* g, bool want_dom) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
     k_walk_cv<<<grid_ilp(n), kBlock, 0, s>>>(n, g->lev, g->strat, g->flags, g->sink0, g->gd, g->gdB, g->gd32, g->ws,
-                                             g->wsB, g->plist, c);
-    prof_end(g, KID_WALK, 1);
+                                             g->wsB, g->hugelist, c);
+    k_walk_more_cv<<<g->coop_blocks, kBlock, 0, s>>>(g->lev, g->hugelist, g->strat, g->sink0, g->gd, g->gdB, g->gd32,
+                                                     g->ws, g->wsB, g->plist, c);
+    prof_end(g, KID_WALK, 2);
     {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;

@@ -21,6 +21,7 @@ namespace pg {
 
 constexpr int kBlock = 256;
 constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
+constexpr int kWalkShort = 8;         // steps of the first walk pass; longer walks continue in a dense second pass
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
 constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
 // Count-vector mode (repeated priorities): at most kMaxLevels distinct
@@ -68,6 +69,7 @@ constexpr uint8_t kKindSinkChild = 2;  // nearest greater ancestor is the sink
 // Device counters of one valuation (reset at its start).
 struct Counters {
     int32_t n_pending;   // walks that ran out of steps (length of the pending list)
+    int32_t n_walk2;     // walks continued by the second walk pass
     int32_t left[3];     // pending vertices left after a jump round (three rotating counters)
     int32_t n_fin;       // finite vertices
     int32_t n_odd;       // vertices reaching an odd cycle (all games)

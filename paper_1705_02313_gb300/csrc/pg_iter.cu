@@ -154,14 +154,26 @@ constexpr int kIlp = 4;
 __device__ inline int64_t warp_tile_base(int64_t tile) { return tile * 32 * kIlp; }
 
 // K1: nearest greater vertex along the play, by a direct walk of at most
-// kWalkCap steps. A walk that returns to its start found the maximum of its
-// cycle; a walk that runs out of steps leaves a jump pointer for k_jump_coop.
+// cap steps; the walks still below their start are appended to a list (the
+// pointer-jumping list). A walk that returns to its start found the maximum
+// of its cycle; a walk that runs out of steps leaves a jump pointer for
+// k_jump_coop.
+__device__ inline uint64_t walk_word(int32_t v, int32_t x, uint32_t d, const int32_t* vgame, const int32_t* gsink,
+                                     int32_t sink0, bool* pend) {
+    *pend = false;
+    if (x > v) return gd_pack(true, false, d, x, x == sink_of(v, vgame, gsink, sink0));  // a larger vertex or the sink
+    if (x == v) return gd_pack(true, true, d, v);                                        // v is its cycle's maximum
+    *pend = true;
+    return gd_pack(false, false, d, x);
+}
+
+template <uint32_t cap>
 __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __restrict__ strat,
                                                  const uint8_t* __restrict__ flags, const int32_t* __restrict__ vgame,
                                                  const int32_t* __restrict__ gsink, int32_t sink0,
                                                  uint64_t* __restrict__ gd, uint32_t* __restrict__ gd32,
-                                                 int32_t* __restrict__ plist, int32_t* __restrict__ sz,
-                                                 int32_t* __restrict__ oddsz, Counters* cnt) {
+                                                 int32_t* __restrict__ more, int32_t* __restrict__ sz,
+                                                 int32_t* __restrict__ oddsz, Counters* cnt, int32_t* more_count) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
             d[j] = 1;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
+        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < cap;
         for (;;) {
             bool any = false;
             int32_t nx[kIlp];
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
                 if (act[j]) {
                     x[j] = nx[j];
                     ++d[j];
-                    act[j] = x[j] < v[j] && d[j] < (uint32_t)kWalkCap;
+                    act[j] = x[j] < v[j] && d[j] < cap;
                 }
                 any |= act[j];
             }
@@ -198,22 +210,15 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
         for (int j = 0; j < kIlp; ++j) {
             bool pend = false;
             if (v[j] < n) {
-                uint64_t w;
-                if (slotid[j]) w = gd_pack(true, false, 0, v[j], true);  // a sink slot: inert
-                else if (x[j] > v[j])                                     // a larger vertex or the sink
-                    w = gd_pack(true, false, d[j], x[j], x[j] == sink_of(v[j], vgame, gsink, sink0));
-                else if (x[j] == v[j]) w = gd_pack(true, true, d[j], v[j]);  // v is the maximum of its cycle
-                else {
-                    w = gd_pack(false, false, d[j], x[j]);
-                    pend = true;
-                }
+                const uint64_t w = slotid[j] ? gd_pack(true, false, 0, v[j], true)  // a sink slot: inert
+                                             : walk_word(v[j], x[j], d[j], vgame, gsink, sink0, &pend);
                 gd[v[j]] = w;
                 gd32[v[j]] = g32_of(w);
                 sz[v[j]] = 0;  // zeros for this valuation's size and odd-total accumulation
                 oddsz[v[j]] = 0;
             }
-            int32_t slot = warp_append(pend, &cnt->n_pending);
-            if (pend) plist[slot] = v[j];
+            int32_t slot = warp_append(pend, more_count);
+            if (pend) more[slot] = v[j];
         }
     }
 }
@@ -1141,8 +1146,9 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     const unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd, g->gd32,
-                                          g->plist, g->sz, g->oddsz, c);
+    // walks here are short but for a few: one pass of kWalkCap steps straight into the jumping list
+    k_walk<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd,
+                                                    g->gd32, g->plist, g->sz, g->oddsz, c, &c->n_pending);
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;

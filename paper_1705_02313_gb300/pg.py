@@ -105,6 +105,7 @@ def lib():
     L.pg_game_info.argtypes = [P, C.POINTER(I32), C.POINTER(I64), C.POINTER(I32)]
     L.pg_game_dummies.argtypes = [P, P]
     L.pg_game_levels.argtypes = [P, C.POINTER(I32), P]
+    L.pg_game_counters.argtypes = [P, C.POINTER(pg_counters)]
     L.pg_solve.argtypes = [P, C.POINTER(pg_solve_opts), C.POINTER(pg_result)]
     L.pg_best_response.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
     L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
@@ -129,7 +130,7 @@ def lib():
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop", "pg_server_create", "pg_server_submit", "pg_server_poll",
-                 "pg_server_fetch", "pg_server_get_stats", "pg_game_levels"]:
+                 "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters"]:
         getattr(L, name).restype = I32
     _lib = L
     return L
@@ -229,6 +230,20 @@ def pg_game_info(game):
     if rc != PG_OK:
         raise PgError(rc, "pg_game_info")
     return n.value, m.value, k.value
+
+
+class pg_counters(C.Structure):
+    _fields_ = [(nm, C.c_int32) for nm in ["n_pending", "jump_rounds", "n_fin", "n_odd", "n_big", "n_huge",
+                                           "n_switch"]]
+
+
+def pg_game_counters(game):
+    """Counters of the last valuation on game (dict)."""
+    c = pg_counters()
+    rc = lib().pg_game_counters(game, C.byref(c))
+    if rc != PG_OK:
+        raise PgError(rc, "pg_game_counters")
+    return {f: getattr(c, f) for f, _ in pg_counters._fields_}
 
 
 def pg_game_levels(game):
