@@ -208,10 +208,31 @@ def cv_measure(name, ctx, steps=3):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # best responses two ways (Section 4 and Table 2): one-player strategy
+    # improvement against Bellman-Ford, from sigma_init and from the final sigma
+    g = pg.pg_load_csr(ctx, n, m, *d_in)
+    br = {}
+    try:
+        sig_final = torch.empty(n, dtype=torch.int32, device="cuda")
+        pg.pg_solve(ctx, g, sigma=sig_final)
+        for label, sig in [("sigma_init", torch.full((n,), -1, dtype=torch.int32, device="cuda")),
+                           ("sigma_final", sig_final)]:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it = pg.pg_best_response(ctx, g, sig)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            rounds = pg.pg_best_response_bf(ctx, g, sig)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            br[label] = {"si_ms": (t1 - t0) * 1e3, "si_iterations": it, "bellman_ford_ms": (t2 - t1) * 1e3,
+                         "bellman_ford_rounds": rounds}
+    finally:
+        pg.pg_game_free(g)
     return {"workload": name, "description": WORKLOADS[name][2], "n": n, "m": m, "levels_of_g_prime": levels.tolist(),
             "major_iterations": major, "valuations_per_solve": inner, "full_solve_ms": ms,
             "edges_per_s": m * inner_total / (ms * steps / 1000.0), "unit": "edges/s",
-            "inner_iteration_us": ms * 1000.0 / inner}
+            "inner_iteration_us": ms * 1000.0 / inner, "best_response": br}
 
 
 # ---------------------------------------------------------------------------

@@ -308,6 +308,19 @@ pg_status pg_server_get_stats(pg_server *server, pg_server_stats *out);
 /* The message of the worker's failure, or "no error". */
 const char *pg_server_error(pg_server *server);
 
+/* Bellman-Ford best response (Section 4, "Computing Best Responses"), the
+ * paper's comparison point for one-player strategy improvement (Table 2):
+ * shortest paths to the sink under the order of Section 3, computed by Jacobi
+ * rounds over all vertices until no value changes. Count-vector mode only
+ * (repeated priorities; PG_EUNSUPPORTED otherwise). Arguments as in
+ * pg_best_response, except that tau_out is output only (nullable; Odd's
+ * choice: the first edge of least value). *rounds_out (nullable) receives the
+ * rounds run. The valuation written to out is that of (sigma, tau_out): the
+ * best-response values, equal to pg_best_response's. PG_ENOTADMISSIBLE when
+ * the values keep decreasing past n + 2 rounds (sigma not admissible). */
+pg_status pg_best_response_bf(pg_game *game, const int32_t *sigma, const int8_t *dummy_sigma, int32_t *tau_out,
+                              int32_t mem_kind, pg_valuation *out, int64_t *rounds_out);
+
 /* Valuation of one successor function without allocating any memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory themselves or let a library do it, for example code

@@ -620,6 +620,38 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
     return PG_OK;
 }
 
+pg_status pg_best_response_bf(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma, int32_t* tau_out,
+                              int32_t mem_kind, pg_valuation* out, int64_t* rounds_out) {
+    if (!g) return PG_EINVAL;
+    pg_ctx* ctx = g->ctx;
+    if (!sigma) return fail(ctx, PG_EINVAL, "pg_best_response_bf: sigma is NULL");
+    if (!g->cv) return fail(ctx, PG_EUNSUPPORTED, "pg_best_response_bf: count-vector mode only (repeated priorities)");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, PG_ECUDA, "cudaSetDevice failed");
+    pg_status st = apply_profile(g, sigma, nullptr, dummy_sigma, mem_kind);
+    if (!st) st = reset_scratch(g);
+    if (st) return st;
+    Timer tm(g);
+    tm.mark(3);
+    int64_t rounds = 0;
+    st = bellman_ford_cv(g, &rounds);
+    if (rounds_out) *rounds_out = rounds;
+    if (st) return st;
+    tm.mark(2);
+    g->t_total = tm.since(3, 2);
+    // the valuation of (sigma, the Bellman-Ford best response) for the outputs
+    st = enqueue_valuation(g, out && out->dom);
+    if (!st) st = sync_counters(g);
+    if (!st) st = write_outputs(g, mem_kind, nullptr, nullptr, tau_out, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (!st && out) {
+        st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, out->val_class, out->val_depth, out->val_rank,
+                           out->dom, nullptr);
+        if (!st && out->val_counts) st = write_counts(g, out->mem_kind, out->val_counts);
+    }
+    if (st) return st;
+    if (g->hcnt->n_odd > 0) return fail(ctx, PG_ENOTADMISSIBLE, "pg_best_response_bf: an odd cycle was reached");
+    return PG_OK;
+}
+
 pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma, const int32_t* tau,
                      int32_t mem_kind, pg_valuation* out) {
     if (!g) return PG_EINVAL;

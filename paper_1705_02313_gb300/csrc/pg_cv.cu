@@ -470,7 +470,117 @@ __global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i12
     }
 }
 
+// Bellman-Ford (Section 4, "Computing Best Responses": a best response is a
+// shortest path to the sink under the order of Section 3; odd priorities are
+// negative weights, and an admissible sigma leaves Odd no negative cycle).
+// One Jacobi round: every vertex takes its weight plus the best key of its
+// successors under the previous round's keys (Odd: the least over its edges;
+// Even: the one sigma names); an unreached vertex stays top.
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_bf_round(int32_t n, Levels L, const OffT* __restrict__ off,
+                                                     const int32_t* __restrict__ tgt,
+                                                     const uint8_t* __restrict__ flags,
+                                                     const int32_t* __restrict__ strat, const i128* __restrict__ src,
+                                                     i128* __restrict__ dst, int32_t* changed) {
+    int32_t ch = 0;
+    const i128 top = top_key();
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        if (f & kSinkSlot) {
+            dst[v] = 0;
+            continue;
+        }
+        i128 best = top;
+        if (f & kOwnerOdd) {
+            for (OffT e = off[v]; e < off[v + 1]; ++e) {
+                const i128 k = src[tgt[e]];
+                if (k < best) best = k;
+            }
+        } else {
+            best = src[strat[v]];
+        }
+        const i128 nk = best == top ? top : weight_of(L, v) + best;
+        ch += nk != src[v];
+        dst[v] = nk;
+    }
+    block_add32(ch, changed);
+}
+
+__global__ void k_bf_init(int32_t n, const uint8_t* __restrict__ flags, i128* __restrict__ key) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        key[v] = (flags[v] & kSinkSlot) ? (i128)0 : top_key();
+}
+
+// Odd's strategy from the final keys: the first edge of least key.
+template <typename OffT>
+__global__ void k_bf_argmin(int32_t n, const OffT* __restrict__ off, const int32_t* __restrict__ tgt,
+                            const uint8_t* __restrict__ flags, const i128* __restrict__ key, int32_t* strat) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        if ((f & kSinkSlot) || !(f & kOwnerOdd)) continue;
+        int32_t best = -1;
+        i128 bk = 0;
+        for (OffT e = off[v]; e < off[v + 1]; ++e) {
+            const i128 k = key[tgt[e]];
+            if (best < 0 || k < bk) {
+                best = tgt[e];
+                bk = k;
+            }
+        }
+        strat[v] = best;
+    }
+}
+
 }  // namespace
+
+// Bellman-Ford best response on g->strat's sigma: rounds until no key
+// changes (checked every kCheck rounds), at most n + 2 rounds (more would
+// mean a negative cycle: sigma not admissible). Leaves Odd's choice in
+// g->strat; *rounds gets the rounds run.
+pg_status bellman_ford_cv(pg_game* g, int64_t* rounds) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int32_t n = g->n;
+    constexpr int kCheck = 8;
+    int32_t* changed = nullptr;
+    PG_CUDA_TRY(ctx, cudaMallocAsync((void**)&changed, sizeof(int32_t) * kCheck, s));
+    int32_t hchg[kCheck];
+    i128* buf[2] = {g->ws, g->wsB};
+    ctx->launches += 1;
+    k_bf_init<<<grid_n(n), kBlock, 0, s>>>(n, g->flags, buf[0]);
+    int64_t r = 0;
+    pg_status st = PG_OK;
+    for (;;) {
+        cudaError_t e = cudaMemsetAsync(changed, 0, sizeof(int32_t) * kCheck, s);
+        for (int i = 0; i < kCheck && e == cudaSuccess; ++i, ++r) {
+            ctx->launches += 1;
+            k_bf_round<int32_t><<<grid_n(n), kBlock, 0, s>>>(n, g->lev, g->off, g->tgt, g->flags, g->strat,
+                                                             buf[r & 1], buf[(r + 1) & 1], changed + i);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hchg, changed, sizeof(hchg), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(ctx, e, "bellman_ford_cv");
+            break;
+        }
+        if (hchg[kCheck - 1] == 0) break;
+        if (r > (int64_t)n + 2) {
+            st = fail(ctx, PG_ENOTADMISSIBLE, "Bellman-Ford: keys still decrease (a negative cycle: sigma is not admissible)");
+            break;
+        }
+    }
+    if (st == PG_OK) {
+        // the keys of the last round are in buf[r & 1]
+        ctx->launches += 1;
+        k_bf_argmin<int32_t><<<grid_n(n), kBlock, 0, s>>>(n, g->off, g->tgt, g->flags, buf[r & 1], g->strat);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "k_bf_argmin");
+    }
+    cudaFreeAsync(changed, s);
+    *rounds = r;
+    return st;
+}
 
 pg_status alloc_cv(pg_game* g) {
     pg_ctx* ctx = g->ctx;

@@ -307,6 +307,8 @@ pg_status alloc_cv(pg_game* g);
 pg_status enqueue_valuation_cv(pg_game* g, bool want_dom);
 pg_status enqueue_switch_cv(pg_game* g, int player);
 pg_status write_counts(pg_game* g, int32_t mem_kind, int32_t* counts);
+// Bellman-Ford best response against the sigma in g->strat (count-vector mode).
+pg_status bellman_ford_cv(pg_game* g, int64_t* rounds);
 }  // namespace pg
 
 #define PG_CUDA_TRY(ctx, expr)                                    \

@@ -106,6 +106,7 @@ def lib():
     L.pg_game_dummies.argtypes = [P, P]
     L.pg_game_levels.argtypes = [P, C.POINTER(I32), P]
     L.pg_game_counters.argtypes = [P, C.POINTER(pg_counters)]
+    L.pg_best_response_bf.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
     L.pg_solve.argtypes = [P, C.POINTER(pg_solve_opts), C.POINTER(pg_result)]
     L.pg_best_response.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation), C.POINTER(I64)]
     L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
@@ -130,7 +131,7 @@ def lib():
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
                  "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop", "pg_server_create", "pg_server_submit", "pg_server_poll",
-                 "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters"]:
+                 "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters", "pg_best_response_bf"]:
         getattr(L, name).restype = I32
     _lib = L
     return L
@@ -300,6 +301,20 @@ def pg_best_response(ctx, game, sigma, tau_inout=None, dummy_sigma=None, val_cla
                                 _same_kind(sigma, tau_inout, dummy_sigma), C.byref(val), C.byref(iters))
     _check(ctx, rc, "pg_best_response")
     return iters.value
+
+
+def pg_best_response_bf(ctx, game, sigma, tau_out=None, dummy_sigma=None, val_class=None, val_depth=None,
+                        val_rank=None, dom=None, val_counts=None):
+    """Bellman-Ford best response (count-vector mode); returns the rounds run."""
+    _dtype_check(sigma, np.int32, "sigma")
+    _dtype_check(tau_out, np.int32, "tau_out")
+    val = pg_valuation(_ptr_kind(val_class)[0], _ptr_kind(val_depth)[0], _ptr_kind(val_rank)[0], _ptr_kind(dom)[0],
+                       _same_kind(val_class, val_depth, val_rank, dom, val_counts), _ptr_kind(val_counts)[0])
+    rounds = C.c_int64(0)
+    rc = lib().pg_best_response_bf(game, _ptr_kind(sigma)[0], _ptr_kind(dummy_sigma)[0], _ptr_kind(tau_out)[0],
+                                   _same_kind(sigma, tau_out, dummy_sigma), C.byref(val), C.byref(rounds))
+    _check(ctx, rc, "pg_best_response_bf")
+    return rounds.value
 
 
 def pg_valuate(ctx, game, sigma=None, tau=None, dummy_sigma=None, val_class=None, val_depth=None, val_rank=None,

@@ -210,3 +210,35 @@ def test_cv_limits(pg, ctx):
     with pytest.raises(pg.PgError) as e:
         pg.pg_load_csr(ctx, n, n, off, tgt, np.zeros(n, np.uint8), (np.arange(n) % 2).astype(np.int32))
     assert e.value.code == pg.PG_EUNSUPPORTED
+
+
+def test_cv_bellman_ford_best_response(pg, ctx):
+    # Bellman-Ford (Section 4) and one-player strategy improvement reach the
+    # same best-response values (shortest paths to the sink are unique in value)
+    for n, levels, seed in [(3000, 3, 1), (30000, 4, 2), (20000, 2, 3)]:
+        g = gen.random_game(n, 2, 5, seed=seed, levels=levels)
+        gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+        for strat0 in [o2.initial_profile(gp), o3.run(gp)["strat"]]:
+            want = o3.run(gp, strat=strat0, mode="best_response")
+            sigma, tau0, dsig = original_profile(gp, strat0)
+            game = pg.pg_load_csr(ctx, g.n, g.m, *g.arrays())
+            try:
+                d = pg.pg_game_levels(game).size
+                out = dict(val_class=np.empty(g.n, np.int8), val_depth=np.empty(g.n, np.int32),
+                           val_counts=np.empty(g.n * d, np.int32))
+                tau = np.empty(g.n, np.int32)
+                rounds = pg.pg_best_response_bf(ctx, game, sigma, tau, dsig, **out)
+            finally:
+                pg.pg_game_free(game)
+            assert 1 <= rounds <= gp["n"] + 8
+            assert np.array_equal(out["val_class"], (want["cls"][: g.n] != 0).astype(np.int8))
+            assert np.array_equal(out["val_counts"].reshape(g.n, d), want["counts"][: g.n])
+            assert np.array_equal(out["val_depth"], want["depth"][: g.n])
+    g = gen.random_game(500, 1, 4, 9)  # distinct priorities: not supported
+    game = pg.pg_load_csr(ctx, g.n, g.m, *g.arrays())
+    try:
+        with pytest.raises(pg.PgError) as e:
+            pg.pg_best_response_bf(ctx, game, np.full(g.n, -1, np.int32))
+        assert e.value.code == pg.PG_EUNSUPPORTED
+    finally:
+        pg.pg_game_free(game)
