@@ -391,22 +391,40 @@ __device__ inline int32_t order_key(int32_t c, bool odd) { return odd ? -(c + 1)
 // Finite children into their segments at the slots taken in k_chain1
 // (order key, subtree size); the sink's children record size and parity for
 // the id-ordered scan. Also clears the children counts for the next valuation.
+// kIlp vertices per thread, their parents' segment offsets gathered together.
 __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* __restrict__ gd32,
                                                     const uint8_t* __restrict__ kind, const int32_t* __restrict__ sz,
                                                     const int32_t* __restrict__ coff, const int32_t* __restrict__ slot,
                                                     int32_t* __restrict__ ccnt, int2* __restrict__ cl_ks,
                                                     int32_t* __restrict__ sinkval) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint8_t kd = kind[v];
-        int32_t sv = 0;
-        ccnt[v] = 0;
-        if (kd & kKFin) {
-            const bool odd = (kd & kKOdd) != 0;
-            const int32_t s = 1 + sz[v];
-            if (kd & kKSinkChild) sv = s | (odd ? INT32_MIN : 0);
-            else cl_ks[coff[g32_ptr(gd32[v])] + slot[v]] = make_int2(order_key(v, odd), s);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], base[kIlp], sl[kIlp], s[kIlp];
+        uint8_t kd[kIlp];
+        bool ent[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            kd[j] = v[j] < n ? kind[v[j]] : 0;
+            ent[j] = (kd[j] & kKFin) && !(kd[j] & kKSinkChild);
+            s[j] = (kd[j] & kKFin) ? 1 + sz[v[j]] : 0;
+            sl[j] = ent[j] ? slot[v[j]] : 0;
+            base[j] = ent[j] ? g32_ptr(gd32[v[j]]) : 0;
         }
-        sinkval[v] = sv;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) base[j] = ent[j] ? coff[base[j]] : 0;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (v[j] >= n) continue;
+            const bool odd = (kd[j] & kKOdd) != 0;
+            ccnt[v[j]] = 0;
+            int32_t sv = 0;
+            if ((kd[j] & kKFin) && (kd[j] & kKSinkChild)) sv = s[j] | (odd ? INT32_MIN : 0);
+            if (ent[j]) cl_ks[base[j] + sl[j]] = make_int2(order_key(v[j], odd), s[j]);
+            sinkval[v[j]] = sv;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ccnt[n] = 0;
 }
@@ -1167,7 +1185,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
     prof_end(g, KID_CSCAN, 3);
     prof_begin(g, KID_SCATTER);
-    k_scatter<<<grid, kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval);
+    k_scatter<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval);
     prof_end(g, KID_SCATTER, 1);
     prof_begin(g, KID_SIBLINGS);
     k_siblings<<<grid, kBlock, 0, s>>>(n, g->coff, g->cl_ks, g->wgt, g->oddsz, g->plist, g->hugelist, c);
