@@ -282,6 +282,7 @@ typedef struct {
     int64_t admitted_while_busy;  /* games admitted while other games were resident */
     int64_t rounds, iterations, max_resident;
     int64_t capacity_vertices, capacity_edges;
+    double loop_ms, repack_ms, collect_ms;  /* worker wall time in rounds, in repacking, in writing results */
 } pg_server_stats;
 
 /* Creates a server on device; opts may be NULL (defaults). */

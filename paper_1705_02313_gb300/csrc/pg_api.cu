@@ -167,6 +167,8 @@ Stage stage_layout(int64_t n0, int64_t k) {
 
 }  // namespace
 
+size_t stage_bytes_for(int64_t n0, int64_t k) { return stage_layout(n0, k).bytes; }
+
 pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
                         int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig, bool depth_ready) {
     pg_ctx* ctx = g->ctx;

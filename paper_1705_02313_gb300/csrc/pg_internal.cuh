@@ -269,6 +269,8 @@ struct Timer {
 // Sets g->strat from a profile in original ids (NULL arrays: the initial profile).
 pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, const int8_t* dsig, int32_t mem_kind);
 // Writes results in original ids (host or device arrays; NULL skips).
+// Bytes of the device staging that write_outputs uses for host outputs.
+size_t stage_bytes_for(int64_t n0, int64_t k);
 // depth_ready: the depth pass already ran after the last valuation.
 pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sigma, int32_t* tau, int8_t* vclass,
                         int32_t* vdepth, int32_t* vrank, int32_t* vdom, int8_t* dsig, bool depth_ready = false);

@@ -139,6 +139,8 @@ struct pg_server {
     pg_game* B = nullptr;  // packed batch at capacity
     int64_t capN = 0, capM = 0;
     int32_t capG = 0;
+    void* stage = nullptr;  // device staging of finished games' outputs (grown as needed)
+    size_t stage_size = 0;
 };
 
 namespace {
@@ -279,12 +281,20 @@ pg_status collect(pg_server* sv, size_t i, Done* d) {
     const int64_t o0 = g->h_base0[i], n0 = g->h_base0[i + 1] - o0;
     const int32_t d0 = g->h_dbase[i], k = g->h_dbase[i + 1] - d0;
     // a view of the packed batch restricted to game i's original vertices and dummies
+    const size_t need = stage_bytes_for(n0, k);
+    if (need > sv->stage_size) {
+        if (sv->stage) cudaFree(sv->stage);
+        sv->stage = nullptr;
+        sv->stage_size = 0;
+        PG_CUDA_TRY(ctx, cudaMalloc(&sv->stage, need + need / 2));
+        sv->stage_size = need + need / 2;
+    }
     pg_game view = *g;
     view.nid0 = g->nid0 + o0;
     view.dnid = g->dnid + d0;
     view.n0 = n0;
     view.k = k;
-    view.stage = nullptr;
+    view.stage = sv->stage;
     d->n = (int32_t)n0;
     d->k = k;
     d->win.resize(n0);
@@ -296,7 +306,6 @@ pg_status collect(pg_server* sv, size_t i, Done* d) {
     d->dsig.resize(std::max(k, 1));
     pg_status st = write_outputs(&view, PG_MEM_HOST, d->win.data(), d->sigma.data(), d->tau.data(), d->cls.data(),
                                  d->depth.data(), d->rank.data(), nullptr, d->dsig.data(), true);
-    if (view.stage) cudaFree(view.stage);  // the view's own staging; the batch's arrays stay
     return st;
 }
 
@@ -410,6 +419,7 @@ void worker_main(pg_server* sv) {
         }
         if (sv->res.empty()) continue;
         pg_status st = PG_OK;
+        double t_rep = now_us();
         if (changed) {
             // profiles of the games already in the batch come out first: the new layout starts from them
             if (sv->packed_count > 0) {
@@ -428,9 +438,11 @@ void worker_main(pg_server* sv) {
                 return;
             }
         }
+        const double t_loop = now_us();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->stats.max_resident = std::max<int64_t>(sv->stats.max_resident, (int64_t)sv->res.size());
+            sv->stats.repack_ms += (t_loop - t_rep) / 1e3;
         }
         // one round over all resident games
         int64_t nmax = 0;
@@ -459,10 +471,12 @@ void worker_main(pg_server* sv) {
                 any_timeout |= gs[i].phase == kPhaseTimeout;
             }
         }
+        const double t_col = now_us();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->stats.rounds += 1;
             sv->stats.iterations += sv->B->t_vals;
+            sv->stats.loop_ms += (t_col - t_loop) / 1e3;
         }
         if (!any_done) continue;
         if (any_timeout) {  // results describe the profile being returned
@@ -518,6 +532,7 @@ void worker_main(pg_server* sv) {
                 sv->done_order.push_back(f.first);
                 sv->stats.completed += 1;
             }
+            sv->stats.collect_ms += (now_us() - t_col) / 1e3;
             sv->cv_done.notify_all();
         }
     }
@@ -593,6 +608,7 @@ void pg_server_destroy(pg_server* sv) {
     for (Resident& r : sv->res) free_game(r.g);
     for (Resident& r : sv->ready) free_game(r.g);
     if (sv->B) free_game(sv->B);
+    if (sv->stage) cudaFree(sv->stage);
     cudaStreamDestroy(sv->ctx->stream);
     cudaStreamDestroy(sv->lctx->stream);
     pg_ctx_destroy(sv->ctx);

@@ -70,7 +70,8 @@ class pg_served(C.Structure):
 class pg_server_stats(C.Structure):
     _fields_ = [(nm, C.c_int64) for nm in ["submitted", "admitted", "completed", "queued", "admitted_while_busy",
                                            "rounds", "iterations", "max_resident", "capacity_vertices",
-                                           "capacity_edges"]]
+                                           "capacity_edges"]] + \
+               [(nm, C.c_double) for nm in ["loop_ms", "repack_ms", "collect_ms"]]
 
 
 class pg_kernel_stat(C.Structure):
