@@ -224,6 +224,7 @@ typedef struct {
     int32_t *status;       /* host, ngames */
     int64_t *dummy_base;   /* host, ngames + 1, out */
     int64_t iterations;    /* out: lockstep iterations run for the whole batch */
+    double load_ms, pack_ms, loop_ms; /* out: wall time loading the games, packing them, and in the loop */
 } pg_result_batch;
 
 /* Solves many games together (Algorithm 1, Section 4, for each): all games

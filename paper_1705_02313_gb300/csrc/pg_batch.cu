@@ -8,6 +8,10 @@
 // follows exactly the trajectory it would follow alone.
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
+#include <thread>
+
 #include "pg_internal.cuh"
 
 namespace pg {
@@ -155,26 +159,78 @@ namespace {
 pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int64_t* eb, const int32_t* offsets,
                       const int32_t* targets, const uint8_t* owner, const int32_t* pri, int32_t mem_kind,
                       int64_t max_inner, pg_result_batch* out) {
+    auto wall = []() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count(); };
+    const double t0 = wall();
     std::vector<pg_game*> games(ngames, nullptr);
     auto cleanup = [&]() {
         for (pg_game* gi : games)
             if (gi) free_game(gi);
     };
+    // Loading (validation, preprocessing, relabelling) is a chain of small
+    // kernels and host synchronisations per game: up to kLoaders threads,
+    // each with its own stream, load games concurrently so that their work
+    // overlaps on the device. The first failing game (in index order) decides
+    // the status.
+    constexpr int kLoaders = 8;
+    const int nload = std::max(1, std::min<int>(kLoaders, ngames));
+    std::vector<pg_ctx*> lctx(nload, nullptr);
+    std::vector<pg_status> gst_load(ngames, PG_OK);
+    std::vector<std::string> gerr(ngames);
+    for (int t = 0; t < nload; ++t) {
+        pg_status st = pg_ctx_create(&lctx[t], ctx->device);
+        if (st == PG_OK && cudaStreamCreateWithFlags(&lctx[t]->stream, cudaStreamNonBlocking) != cudaSuccess)
+            st = PG_ECUDA;
+        if (st) {
+            for (pg_ctx* c : lctx)
+                if (c) {
+                    if (c->stream) cudaStreamDestroy(c->stream);
+                    pg_ctx_destroy(c);
+                }
+            return fail(ctx, st, "pg_solve_batch: could not create loader streams");
+        }
+    }
+    std::atomic<int32_t> next(0);
+    auto loader = [&](int t) {
+        cudaSetDevice(ctx->device);
+        for (;;) {
+            const int32_t i = next.fetch_add(1);
+            if (i >= ngames) break;
+            const int64_t ni = vb[i + 1] - vb[i], mi = eb[i + 1] - eb[i];
+            pg_status st = load_game(lctx[t], (int32_t)ni, mi, offsets + vb[i] + i, targets + eb[i], owner + vb[i],
+                                     pri + vb[i], mem_kind, &games[i], false);
+            if (st == PG_OK && games[i]->cv) {
+                st = fail(lctx[t], PG_EUNSUPPORTED,
+                          "pg_solve_batch: games with repeated priorities are solved one at a time");
+            }
+            if (st) {
+                gst_load[i] = st;
+                gerr[i] = lctx[t]->err;
+                next.store(ngames);  // stop the other loaders early
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nload; ++t) th.emplace_back(loader, t);
+    loader(0);
+    for (auto& x : th) x.join();
+    for (pg_ctx* c : lctx) {
+        cudaStreamDestroy(c->stream);
+        pg_ctx_destroy(c);
+    }
     int64_t nmax = 0;
     for (int32_t i = 0; i < ngames; ++i) {
-        const int64_t ni = vb[i + 1] - vb[i], mi = eb[i + 1] - eb[i];
-        pg_status st = load_game(ctx, (int32_t)ni, mi, offsets + vb[i] + i, targets + eb[i], owner + vb[i], pri + vb[i],
-                                 mem_kind, &games[i], false);
-        if (st) {
+        if (gst_load[i] != PG_OK) {
             cleanup();
-            return st;
+            ctx->err = gerr[i];
+            return gst_load[i];
         }
-        if (games[i]->cv) {
+        if (!games[i]) {  // not reached because another game failed first
             cleanup();
-            return fail(ctx, PG_EUNSUPPORTED, "pg_solve_batch: games with repeated priorities are solved one at a time");
+            return fail(ctx, PG_ECUDA, "pg_solve_batch: a game was not loaded");
         }
         nmax = std::max<int64_t>(nmax, games[i]->n);
     }
+    const double t1 = wall();
     pg_game* g = nullptr;
     pg_status st = pack_games(ctx, games.data(), ngames, &g);
     if (st) {
@@ -191,8 +247,12 @@ pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int6
     if (st) return st;
     Timer tm(g);
     tm.mark(3);
+    const double t2 = wall();
     st = run_loop(g, cap, true, tm);
     if (st) return st;
+    out->load_ms = t1 - t0;
+    out->pack_ms = t2 - t1;
+    out->loop_ms = wall() - t2;
     std::vector<GameState> gs(ngames);
     PG_CUDA_TRY(ctx, cudaMemcpy(gs.data(), g->gst, sizeof(GameState) * ngames, cudaMemcpyDeviceToHost));
     bool any_timeout = false, any_odd = false;

@@ -54,7 +54,8 @@ class pg_result_batch(C.Structure):
     _fields_ = [("win", C.c_void_p), ("sigma", C.c_void_p), ("tau", C.c_void_p), ("val_class", C.c_void_p),
                 ("val_depth", C.c_void_p), ("val_rank", C.c_void_p), ("dummy_sigma", C.c_void_p),
                 ("mem_kind", C.c_int32), ("major", C.c_void_p), ("inner", C.c_void_p), ("status", C.c_void_p),
-                ("dummy_base", C.c_void_p), ("iterations", C.c_int64)]
+                ("dummy_base", C.c_void_p), ("iterations", C.c_int64), ("load_ms", C.c_double),
+                ("pack_ms", C.c_double), ("loop_ms", C.c_double)]
 
 
 class pg_server_opts(C.Structure):
@@ -354,7 +355,8 @@ def pg_solve_batch(ctx, ngames, vtx_base, edge_base, offsets, targets, owner, pr
                               C.byref(res))
     if rc not in (PG_OK, PG_ETIMEOUT, PG_ENOTADMISSIBLE):
         _check(ctx, rc, "pg_solve_batch")
-    return dict(rc=rc, major=major, inner=inner, status=status, dummy_base=dbase, iterations=res.iterations)
+    return dict(rc=rc, major=major, inner=inner, status=status, dummy_base=dbase, iterations=res.iterations,
+                load_ms=res.load_ms, pack_ms=res.pack_ms, loop_ms=res.loop_ms)
 
 
 def pack_games(games):
