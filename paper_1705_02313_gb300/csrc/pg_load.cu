@@ -202,9 +202,12 @@ __global__ void k_maps(int32_t n0, int32_t k, const int32_t* nid, int32_t* nid0,
     }
 }
 
+// The game's own arrays, stream-ordered on the load stream (no global
+// allocation lock between concurrent loads); the load synchronises its
+// stream before returning, so they are valid on every stream afterwards.
 template <typename T>
-cudaError_t dalloc(T** p, int64_t count) {
-    return cudaMalloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T));
+cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
+    return cudaMallocAsync((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
 }
 
 // Temporaries of one load, stream-ordered on the load's stream (allocating
@@ -357,16 +360,16 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         cudaError_t _e = (expr);                      \
         if (_e != cudaSuccess) return bail(_e, #expr); \
     } while (0)
-    LG_TRY(dalloc(&g->off, np + 2));
-    LG_TRY(dalloc(&g->tgt, mp));
-    LG_TRY(dalloc(&g->flags, np + 1));
-    LG_TRY(dalloc(&g->pri, np + 1));
-    LG_TRY(dalloc(&g->nid0, n));
-    LG_TRY(dalloc(&g->orig_of, np + 1));
-    LG_TRY(dalloc(&g->dnid, k));
-    LG_TRY(dalloc(&g->dummy_of, k));
-    LG_TRY(dalloc(&g->strat, np + 1));
-    LG_TRY(dalloc(&g->gsink, 1));
+    LG_TRY(dalloc(&g->off, np + 2, s));
+    LG_TRY(dalloc(&g->tgt, mp, s));
+    LG_TRY(dalloc(&g->flags, np + 1, s));
+    LG_TRY(dalloc(&g->pri, np + 1, s));
+    LG_TRY(dalloc(&g->nid0, n, s));
+    LG_TRY(dalloc(&g->orig_of, np + 1, s));
+    LG_TRY(dalloc(&g->dnid, k, s));
+    LG_TRY(dalloc(&g->dummy_of, k, s));
+    LG_TRY(dalloc(&g->strat, np + 1, s));
+    LG_TRY(dalloc(&g->gsink, 1, s));
     ++ctx->launches;
     k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
 
