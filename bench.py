@@ -149,6 +149,19 @@ def algorithmic_bytes(name, s):
     return table.get(name)
 
 
+def kernel_entry(name, v, s, hbm):
+    """Per kernel class: device ms over the timed solve, launches, calls, and
+    algorithmic GB/s per call against the measured HBM copy bandwidth."""
+    ms, launches, calls = v
+    e = {"ms": ms, "launches": launches, "calls": calls}
+    # the Even pass returns at once in iterations where Odd switched: per call it has no fixed work
+    ab = algorithmic_bytes(name, s) if name != "switch_even" else None
+    if ab and calls and ms > 0:
+        gbs = ab / (ms / calls / 1000.0) / 1e9
+        e.update(us_per_call=ms / calls * 1000.0, algorithmic_bytes=ab, achieved_gbs=gbs, frac_of_hbm=gbs / hbm)
+    return e
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_1705_02313_gb300", "csrc"))):
@@ -170,6 +183,38 @@ def measured_traffic(kernel, workload):
         return e["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+# ---------------------------------------------------------------------------
+# one long successor chain: the valuation alone (nearest-greater walks that run
+# out of steps, pointer jumping, ranks along an n-long list)
+
+def chain_measure(n, ctx, reps=3):
+    import torch
+
+    from paper_1705_02313_gb300 import gen, pg
+    g, sigma = gen.chain_profile(n, seed=7)
+    d_in = [torch.from_numpy(a).cuda() for a in g.arrays()]
+    d_sig = torch.from_numpy(sigma).cuda()
+    game = pg.pg_load_csr(ctx, g.n, g.m, *d_in)
+    try:
+        vr = torch.empty(n, dtype=torch.int32, device="cuda")
+        pg.pg_valuate(ctx, game, d_sig, None, None, val_rank=vr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            pg.pg_valuate(ctx, game, d_sig, None, None, val_rank=vr)
+        e1.record()
+        torch.cuda.synchronize()
+        c = pg.pg_game_counters(game)
+    finally:
+        pg.pg_game_free(game)
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "chain-%d" % n, "description": "one successor chain through all %d vertices (an all-Even game, "
+            "chain along a random permutation, one extra random edge per vertex), valuation only" % n,
+            "valuation_ms": ms, "pending_walks": c["n_pending"], "jump_rounds": c["jump_rounds"],
+            "vertices_per_s": n / (ms / 1000.0)}
 
 
 # ---------------------------------------------------------------------------
@@ -589,7 +634,7 @@ def run_ours(args):
         "wall_s": wall,
         "roofline": roof,
         "inner_iteration": valuation_path,
-        "kernels": {nm: {"ms": v[0], "launches": v[1], "calls": v[2]} for nm, v in kstats.items() if v[1]},
+        "kernels": {nm: kernel_entry(nm, v, s, hbm) for nm, v in kstats.items() if v[1]},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -609,6 +654,8 @@ def run_ours(args):
                             "note": "SI-Reset: every best response restarts from the first edge of each Odd list"}
     if rank == 0 and args.cv_workload:
         line["count_vector"] = cv_measure(args.cv_workload, ctx)
+    if rank == 0 and args.chain > 0:
+        line["long_chain"] = chain_measure(args.chain, ctx)
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_measure(args.batch)
     if rank == 0 and args.serve > 0:
@@ -669,6 +716,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-one-at-a-time measurement")
+    ap.add_argument("--chain", type=int, default=0,
+                    help="also time pg_valuate on one successor chain of this many vertices (0: skip)")
     ap.add_argument("--cv-workload", default="random-10m-4pri",
                     help="count-vector workload measured beside the main line ('' to skip)")
     ap.add_argument("--serve", type=float, default=10.0,
