@@ -969,7 +969,8 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
         const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : 0;
         int32_t best = player == 0 ? sk : -1;
         int32_t bk = player == 0 ? key[sk] : INT32_MAX;
-        const int32_t curkey = key[cur];
+        // the current successor is the sink (Even) or one of the edges: its key comes with them
+        int32_t curkey = (player == 0 && cur == sk) ? bk : 0;
         for (int64_t e = e0; e < e1; e += 4) {
             int32_t t[4], kk[4];
 #pragma unroll
@@ -979,6 +980,7 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (t[j] < 0) continue;
+                if (t[j] == cur) curkey = kk[j];
                 bool better = player == 0 ? kk[j] > bk : (best < 0 || kk[j] < bk);
                 if (better) {
                     best = t[j];
