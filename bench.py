@@ -294,7 +294,7 @@ BATCHES = {
 }
 
 
-def batch_measure(name):
+def batch_measure(name, cpu_budget=0):
     """Solves the batch three ways, each once after a warm-up on its first
     games: pg_solve_batch with the inputs already in device memory, the same
     from host arrays with results copied back (end to end), and a loop of
@@ -347,6 +347,17 @@ def batch_measure(name):
     finally:
         pg.pg_ctx_destroy(ctx)
     inner = res["inner"]
+    cpu = None
+    if cpu_budget > 0:
+        c = cpu_batch(count, lo, hi, dmin, dmax, cpu_budget)
+        k = c["games"]
+        oracle_same = all(np.array_equal(c["win"][i], win_b[vb[i]:vb[i + 1]]) and
+                          np.array_equal(c["sigma"][i], sig_b[vb[i]:vb[i + 1]]) for i in range(k))
+        cpu = {"value": k / c["seconds"], "unit": "games/s", "cores": c["cores"], "kind": "oracle",
+               "sample": "games 0..%d of the batch (%d vertices), one game per process on %d processes, %.1f s wall "
+                         "(%.1f s of single-thread solves); each worker generates its game before timing the solve"
+                         % (k - 1, c["vertices"], c["cores"], c["seconds"], c["solve_seconds"]),
+               "identical_to_gpu": bool(oracle_same)}
     return {"workload": name, "description": desc, "games": count, "vertices": n0, "edges": m0,
             "metric": "batched games/s vs one-at-a-time", "unit": "games/s",
             "batched_games_per_s": count / t_batch, "batched_e2e_games_per_s": count / t_e2e,
@@ -354,7 +365,7 @@ def batch_measure(name):
             "batched_s": t_batch, "batched_e2e_s": t_e2e, "one_at_a_time_s": t_single,
             "lockstep_iterations": int(res["iterations"]), "inner_min": int(inner.min()),
             "inner_max": int(inner.max()), "valuations_one_at_a_time": int(inner_sum),
-            "generate_s": t_gen, "identical_results": same,
+            "generate_s": t_gen, "identical_results": same, "cpu_baseline": cpu,
             "timing": "wall clock around each call, device synchronised; includes loading and preprocessing"}
 
 
@@ -369,7 +380,7 @@ SERVE = {
 }
 
 
-def serve_measure(name, seconds):
+def serve_measure(name, seconds, cpu_budget=0):
     """Submits arrivals of a Poisson process for ``seconds`` from one thread,
     polls results from another, then solves the pool one game at a time
     (pg_load_csr + pg_solve from host arrays) for comparison."""
@@ -434,6 +445,13 @@ def serve_measure(name, seconds):
     t_single = time.perf_counter() - t0
     pg.pg_ctx_destroy(ctx)
     torch.cuda.synchronize()
+    cpu = None
+    if cpu_budget > 0:
+        c = cpu_batch(P, cfg["lo"], cfg["hi"], cfg["dmin"], cfg["dmax"], cpu_budget)
+        cpu = {"value": c["games"] / c["seconds"], "unit": "games/s", "cores": c["cores"], "kind": "oracle",
+               "sample": "games 0..%d of the pool (%d vertices), one game per process on %d processes, %.1f s wall "
+                         "(%.1f s of single-thread solves)"
+                         % (c["games"] - 1, c["vertices"], c["cores"], c["seconds"], c["solve_seconds"])}
     return {"workload": name, "description": cfg["desc"], "seconds": seconds, "arrivals": int(len(arrivals)),
             "completed": len(done), "ok": ok, "metric": "served games/s and latency", "unit": "games/s",
             "served_games_per_s": served, "offered_games_per_s": len(arrivals) / seconds,
@@ -442,7 +460,7 @@ def serve_measure(name, seconds):
             "queue_ms_p50": float(np.percentile(qus, 50)) if qus.size else None,
             "one_at_a_time_games_per_s": P / t_single, "pool_games": P,
             "pool_vertices": int(vb[-1]), "pool_edges": int(eb[-1]), "generate_s": t_gen,
-            "server": stats, "submit_errors": submit_err,
+            "server": stats, "submit_errors": submit_err, "cpu_baseline": cpu,
             "timing": "wall clock; latency from submission to result, measured by the server"}
 
 
@@ -456,6 +474,40 @@ def cpu_sample(game, iters):
     res = o2.run(gp, max_inner=iters, allow_timeout=True)
     dt = time.perf_counter() - t0
     return dict(seconds=dt, iters=res["inner"], edges=game.m)
+
+
+def _oracle_batch_game(job):
+    """One game of a batch solved by the oracle in a pool worker: generated
+    from its seed, then preprocessed and solved (O-2, single thread)."""
+    i, n, dmin, dmax = job
+    from oracle import o2
+    from paper_1705_02313_gb300 import gen
+    g = gen.native_random_game(n, dmin, dmax, gen.batch_seed(i), nthreads=1)
+    t0 = time.perf_counter()
+    _, res, out = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
+    return i, time.perf_counter() - t0, np.asarray(out["win"], np.uint8), np.asarray(out["sigma"], np.int32)
+
+
+def cpu_batch(count, lo, hi, dmin, dmax, budget_vertices):
+    """The oracle on all host cores, one game per process (spawned), over the
+    first games of the batch up to ``budget_vertices`` vertices in total."""
+    import multiprocessing as mp
+
+    from paper_1705_02313_gb300 import gen
+    sizes = gen.log_uniform_sizes(count, lo, hi).astype(np.int64)
+    take = max(1, int(np.searchsorted(np.cumsum(sizes), budget_vertices, side="right")))
+    take = min(take, count)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    jobs = [(i, int(sizes[i]), dmin, dmax) for i in range(take)]
+    jobs.sort(key=lambda j: -j[1])  # largest first: less idle time at the end
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_batch_game, [(0, 1000, dmin, dmax)] * cores)  # start-up and library load
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_batch_game, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    res.sort(key=lambda r: r[0])
+    return dict(games=take, vertices=int(sizes[:take].sum()), cores=cores, seconds=wall,
+                solve_seconds=float(sum(r[1] for r in res)), win=[r[2] for r in res], sigma=[r[3] for r in res])
 
 
 # ---------------------------------------------------------------------------
@@ -657,9 +709,9 @@ def run_ours(args):
     if rank == 0 and args.chain > 0:
         line["long_chain"] = chain_measure(args.chain, ctx)
     if rank == 0 and not args.no_batch:
-        line["batch"] = batch_measure(args.batch)
+        line["batch"] = batch_measure(args.batch, 0 if args.no_cpu_baseline else args.batch_cpu_vertices)
     if rank == 0 and args.serve > 0:
-        line["serve"] = serve_measure("serve-200", args.serve)
+        line["serve"] = serve_measure("serve-200", args.serve, 0 if args.no_cpu_baseline else args.serve_cpu_vertices)
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_sample(game, args.cpu_iters)
         line["cpu_baseline"] = {"value": r["edges"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -713,6 +765,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random-10m")
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--batch-cpu-vertices", type=int, default=6_000_000,
+                    help="vertices of the batch's first games that the all-cores oracle baseline solves")
+    ap.add_argument("--serve-cpu-vertices", type=int, default=4_000_000,
+                    help="vertices of the serving pool's first games that the all-cores oracle baseline solves")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-one-at-a-time measurement")
