@@ -47,14 +47,29 @@ __global__ void k_validate(int32_t n, int64_t m, const int32_t* off, const int32
 }
 
 // Marks every priority in a bitmap; a bit already set means a repeated priority.
+// The lanes of a warp that mark the same word combine their bits first (one
+// atomic per word and warp), and a word that already holds all of them takes no
+// atomic at all: with few distinct priorities every vertex marks one of a few
+// words, which would otherwise serialise n atomics on them.
 __global__ void k_mark_priorities(int32_t n, const int32_t* pri, int32_t shift_orig, int32_t n_orig,
                                   uint32_t* bits, LoadScalars* sc, int dummy_zero) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += stride) {  // uniform per block
+        const int64_t v = v0 + threadIdx.x;
+        const bool ok = v < n;
         // vertices below n_orig are original (priority shifted by shift_orig); the rest are dummies with 2j (0)
-        int64_t p = v < n_orig ? (int64_t)pri[v] + shift_orig : (dummy_zero ? 0 : 2 * (v - n_orig));
-        uint32_t bit = 1u << (p & 31);
-        uint32_t old = atomicOr(&bits[p >> 5], bit);
-        if (old & bit) atomicOr(&sc->err, kEDup);
+        int64_t p = !ok ? 0 : v < n_orig ? (int64_t)pri[v] + shift_orig : (dummy_zero ? 0 : 2 * (v - n_orig));
+        const uint64_t word = ok ? (uint64_t)(p >> 5) : ~0ull;
+        const uint32_t bit = ok ? 1u << (p & 31) : 0u;
+        const unsigned peers = __match_any_sync(0xffffffffu, word);
+        const uint32_t all = __reduce_or_sync(peers, bit);
+        if (!ok || lane != __ffs(peers) - 1) continue;
+        bool dup = __popc(all) < __popc(peers);  // two lanes of this warp share a priority
+        const uint32_t cur = *(volatile uint32_t*)&bits[word];
+        if ((cur & all) != 0) dup = true;
+        if ((cur & all) != all) dup |= (atomicOr(&bits[word], all) & all) != 0;
+        if (dup && !(*(volatile int32_t*)&sc->err & kEDup)) atomicOr(&sc->err, kEDup);
     }
 }
 
