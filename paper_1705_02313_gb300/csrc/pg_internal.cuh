@@ -215,6 +215,7 @@ struct pg_game {
     void* scan_tmp = nullptr;    // children-count scan scratch
     size_t scan_tmp_bytes = 0;
     int coop_blocks = 0;         // co-resident blocks for the cooperative kernels
+    int chain1_blocks = 0;       // k_chain1 blocks resident at once (0: one block per 8 tiles)
     void* stage = nullptr;       // staging for host outputs
     int64_t* loop_iters = nullptr;  // [1] iterations run by the device-side loop
     // instantiated loop graphs: [0] inner loop only, [1] both players; built for loop_cap[i]
@@ -290,6 +291,7 @@ pg_status reset_games(pg_game* g);
 void free_game(pg_game* g);
 // Co-resident blocks of the cooperative valuation kernels on a device.
 pg_status coop_blocks_for(pg_ctx* ctx, int* out);
+pg_status chain1_blocks_for(pg_ctx* ctx, int* out);
 // per-kernel timing: events around a kernel class on the game's stream
 void prof_begin(pg_game* g, int id);
 void prof_end(pg_game* g, int id, int nlaunch);

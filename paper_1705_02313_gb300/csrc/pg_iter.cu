@@ -1123,6 +1123,8 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A(&g->scan_tmp, g->scan_tmp_bytes));
     pg_status st = coop_blocks_for(ctx, &g->coop_blocks);
     if (st) return st;
+    st = chain1_blocks_for(ctx, &g->chain1_blocks);
+    if (st) return st;
     if (g->cv) {
         pg_status st2 = alloc_cv(g);
         if (st2) return st2;
@@ -1138,6 +1140,17 @@ pg_status coop_blocks_for(pg_ctx* ctx, int* out) {
     PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump_coop, kBlock, 0));
     PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_idscan_coop, kBlock, 0));
     *out = sms * std::max(1, std::min(std::min(a, b), 4));
+    return PG_OK;
+}
+
+// k_chain1 runs as one wave of resident blocks whose warps stride over the
+// tiles: the walks' lengths vary, and a warp with many tiles averages them out,
+// where one tile per warp would hold each block until its longest walk ends.
+pg_status chain1_blocks_for(pg_ctx* ctx, int* out) {
+    int sms = 0, a = 0;
+    PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_chain1, kBlock, 0));
+    *out = sms * std::max(1, a);
     return PG_OK;
 }
 
@@ -1180,8 +1193,9 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         prof_end(g, KID_JUMP, 1);
     }
     prof_begin(g, KID_CHAIN1);
-    k_chain1<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls,
-                                            g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c);
+    const unsigned c1grid = g->chain1_blocks > 0 ? std::min(ilp_grid(n), (unsigned)g->chain1_blocks) : ilp_grid(n);
+    k_chain1<<<c1grid, kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls,
+                                       g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c);
     prof_end(g, KID_CHAIN1, 1);
     prof_begin(g, KID_CSCAN);
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));

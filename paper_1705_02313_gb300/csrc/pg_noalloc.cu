@@ -68,6 +68,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 unsigned char* g_static_addr[kMaxDevices] = {};
 int g_static_coop[kMaxDevices] = {};
+int g_static_chain1[kMaxDevices] = {};
 std::mutex g_static_mu;
 Counters g_static_hcnt;  // host copy of the counters (pageable, fixed)
 
@@ -98,20 +99,22 @@ __global__ void k_static_results(int32_t n, const uint8_t* __restrict__ cls, con
 }
 
 // Device address of the static buffer on the current device (first call per device).
-pg_status static_setup(pg_ctx* ctx, unsigned char** base, int* coop) {
+pg_status static_setup(pg_ctx* ctx, unsigned char** base, int* coop, int* chain1) {
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return PG_EUNSUPPORTED;
     if (!g_static_addr[ctx->device]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || p == nullptr) return PG_ECUDA;
-        int cb = 0;
-        if (coop_blocks_for(ctx, &cb) != PG_OK) return PG_ECUDA;
+        int cb = 0, c1 = 0;
+        if (coop_blocks_for(ctx, &cb) != PG_OK || chain1_blocks_for(ctx, &c1) != PG_OK) return PG_ECUDA;
         g_static_coop[ctx->device] = cb;
+        g_static_chain1[ctx->device] = c1;
         g_static_addr[ctx->device] = (unsigned char*)p;
     }
     *base = g_static_addr[ctx->device];
     *coop = g_static_coop[ctx->device];
+    *chain1 = g_static_chain1[ctx->device];
     return PG_OK;
 }
 
@@ -132,8 +135,8 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     ctx.stream = (cudaStream_t)stream;
     ctx.quiet = true;
     unsigned char* base = nullptr;
-    int coop = 0;
-    pg_status st = static_setup(&ctx, &base, &coop);
+    int coop = 0, chain1 = 0;
+    pg_status st = static_setup(&ctx, &base, &coop, &chain1);
     if (st != PG_OK) return st;
 
     // a game view over the static buffer: only the fields the valuation reads
@@ -170,6 +173,7 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     g.scan_tmp = base + kLayout.scan;
     g.scan_tmp_bytes = kLayout.bytes - kLayout.scan;
     g.coop_blocks = coop;
+    g.chain1_blocks = chain1;
 
     cudaStream_t s = ctx.stream;
     if (cudaMemsetAsync(g.cnt, 0, sizeof(Counters), s) != cudaSuccess) return PG_ECUDA;
