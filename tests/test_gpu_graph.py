@@ -83,6 +83,26 @@ def test_graph_loop_iteration_cap(pg, ctx):
         assert np.array_equal(out_g[k], out_h[k]), k
 
 
+def test_iteration_cap_matches_oracle_at_every_cap(pg, ctx):
+    # at every cap, across Odd and Even switching rounds, the returned profile
+    # is the oracle's after as many valuations, and the returned valuation is
+    # the oracle's valuation of that profile
+    g = gen.random_game(4000, 2, 5, 21)
+    gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+    total = o2.run(gp)["inner"]
+    assert total > 5
+    for cap in range(1, total + 1):
+        rc, _, _, used, it, out = solve(pg, ctx, g, True, max_inner=cap)
+        r = o2.run(gp, max_inner=cap, allow_timeout=True)
+        assert rc == r["status"] == (pg.PG_OK if cap == total else pg.PG_ETIMEOUT), cap
+        assert used and it == cap
+        sigma, tau, dsig = profile_to_original(gp, r["strat"])
+        want = o2.map_back(gp, dict(o2.valuate(gp, r["strat"]), strat=r["strat"]))
+        want.update(sigma=sigma, tau=tau, dummy_sigma=dsig)
+        for k in KEYS + ["dummy_sigma"]:
+            assert np.array_equal(out[k][: len(want[k])], np.asarray(want[k])), (cap, k)
+
+
 def test_graph_reused_across_calls(pg, ctx):
     # a second solve on the same loaded game reuses its graph and agrees
     g = gen.random_game(3000, 2, 6, 4)
