@@ -52,11 +52,33 @@ def switch_keys(gp, val):
     return key
 
 
-def stopping_violations(gp, strat, val):
-    """(Odd vertices with a strictly better edge, Even vertices with a
-    strictly better edge or sink) under the valuation ``val`` of ``strat``."""
+def count_vector_keys(gp, val):
+    """Switching key of every id of G' plus the sink for count-vector
+    valuations (Section 3): a dense rank in the order where TOP is above
+    every finite valuation and two finite ones compare at the highest
+    priority whose counts differ (more is better for an even priority, fewer
+    for an odd one); equal count vectors get equal keys."""
     n = gp["n"]
-    key = switch_keys(gp, val)
+    lp = np.asarray(val["level_pri"], np.int64)
+    counts = np.vstack([np.asarray(val["counts"], np.int64), np.zeros((1, lp.size), np.int64)])
+    top = np.append(np.asarray(val["cls"]) != o2.FIN, False).astype(np.int64)
+    signed = counts * np.where(lp % 2 == 0, 1, -1)[None, :]
+    cols = [signed[:, j] for j in range(lp.size)] + [top]  # lexsort: the last key is the primary one
+    order = np.lexsort(cols)
+    sk = np.stack(cols, axis=1)[order]
+    new = np.ones(n + 1, bool)
+    new[1:] = np.any(sk[1:] != sk[:-1], axis=1)
+    key = np.empty(n + 1, np.int64)
+    key[order] = np.cumsum(new) - 1
+    return key
+
+
+def stopping_violations(gp, strat, val, key=None):
+    """(Odd vertices with a strictly better edge, Even vertices with a
+    strictly better edge or sink) under the valuation ``val`` of ``strat``
+    (``key``: switching keys, by default the ranks of ``val``)."""
+    n = gp["n"]
+    key = switch_keys(gp, val) if key is None else key
     kt = key[gp["tgt"]]
     starts = gp["off"][:-1]
     lo = np.minimum.reduceat(kt, starts)
@@ -85,4 +107,24 @@ def certify(gp, offsets, targets, out):
             bad = np.nonzero(a != b)[0]
             raise AssertionError("%s differs at %d vertices, first %s: got %s want %s" %
                                  (k, bad.size, bad[:5], a[bad[:5]], b[bad[:5]]))
+    return val
+
+
+def certify_counts(gp, offsets, targets, out):
+    """certify() for games whose priorities repeat: the oracle's count-vector
+    valuation (O-3) of the reported profile, the stopping condition under
+    the count-vector order, and the reported count vectors."""
+    from oracle import o3
+    strat = profile_to_gprime(gp, offsets, targets, out["sigma"], out["tau"], out["dummy_sigma"])
+    val = o3.valuate(gp, strat)
+    assert val["status"] == o3.OK and not np.any(val["cls"] == o3.ODDCYCLE), "the profile reaches an odd cycle"
+    bad_odd, bad_even = stopping_violations(gp, strat, val, count_vector_keys(gp, val))
+    assert bad_odd.size == 0, "Odd can still switch at %d vertices, first %s" % (bad_odd.size, bad_odd[:5])
+    assert bad_even.size == 0, "Even can still switch at %d vertices, first %s" % (bad_even.size, bad_even[:5])
+    want = o3.map_back(gp, dict(val, strat=strat))
+    for k in ("win", "sigma", "tau", "val_class", "val_depth", "val_counts"):
+        a, b = np.asarray(out[k]), np.asarray(want[k])
+        if not np.array_equal(a, b):
+            bad = np.nonzero(np.any((a != b).reshape(a.shape[0], -1), axis=1))[0]
+            raise AssertionError("%s differs at %d vertices, first %s" % (k, bad.size, bad[:5]))
     return val

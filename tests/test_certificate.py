@@ -68,3 +68,43 @@ def test_profile_before_the_end_is_rejected():
     val = o2.valuate(gp, r["strat"])
     bad_odd, bad_even = cert.stopping_violations(gp, r["strat"], val)
     assert bad_odd.size + bad_even.size > 0
+
+
+def test_count_vector_keys_follow_the_order():
+    # the dense keys agree with the definitional comparison of O-1 (literal
+    # Maxdiff on count vectors) on every pair of a small game's vertices
+    from oracle import o1, o3
+    g = gen.random_game(60, 1, 3, 11, levels=3)
+    gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+    r = o3.run(gp, max_inner=2, allow_timeout=True)
+    val = o3.valuate(gp, r["strat"])
+    key = cert.count_vector_keys(gp, val)
+    lp = list(val["level_pri"])
+
+    def o1_val(v):
+        if val["cls"][v] != o3.FIN:
+            return (o1.TOP, {}, 0)
+        return (o1.FIN, {int(lp[j]): int(c) for j, c in enumerate(val["counts"][v]) if c}, int(val["depth"][v]))
+
+    vals = [o1_val(v) for v in range(gp["n"])] + [(o1.FIN, {}, 0)]
+    for a in range(gp["n"] + 1):
+        for b in range(gp["n"] + 1):
+            c = o1.compare(vals[a], vals[b])
+            assert int(key[a] > key[b]) - int(key[a] < key[b]) == c, (a, b)
+
+
+@pytest.mark.parametrize("levels", [2, 3, 4])
+def test_count_vector_solutions_are_certified(levels):
+    from oracle import o3
+    g = gen.random_game(5000, 2, 5, 30 + levels, levels=levels)
+    gp, res, out = o3.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
+    out["dummy_sigma"] = (res["strat"][gp["n_orig"]:] != gp["n"]).astype(np.int8)
+    cert.certify_counts(gp, g.offsets, g.targets, out)
+    bad = dict(out, val_counts=out["val_counts"].copy())
+    bad["val_counts"][7, 0] += 1
+    with pytest.raises(AssertionError):
+        cert.certify_counts(gp, g.offsets, g.targets, bad)
+    r = o3.run(gp, max_inner=2, allow_timeout=True)
+    val = o3.valuate(gp, r["strat"])
+    bo, be = cert.stopping_violations(gp, r["strat"], val, cert.count_vector_keys(gp, val))
+    assert bo.size + be.size > 0

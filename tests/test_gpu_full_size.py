@@ -1,5 +1,6 @@
-"""Parity at the full size of the benchmark's workload: the 10,000,000-vertex
-random game (out-degree U[2,5], owners p = 0.5, permuted priorities, seed 0),
+"""Parity at the full size of the benchmark's workloads: the 10,000,000-vertex
+random game (out-degree U[2,5], owners p = 0.5, permuted priorities, seed 0)
+and the same game with priorities uniform over 0..3 (count-vector mode),
 loaded from device arrays and solved to device arrays through the C ABI, as
 the benchmark does (the loop as one CUDA graph).
 
@@ -11,12 +12,13 @@ the benchmark does (the loop as one CUDA graph).
   strictly better edge, which is where Algorithm 1 stops and makes the
   profile optimal (Theorem 1), so the winning regions are certified.
 
-The oracle takes about half a minute here (preprocessing, four valuations).
+The oracles take about half a minute per game (preprocessing, four
+valuations).
 """
 import numpy as np
 import pytest
 
-from oracle import o2
+from oracle import o2, o3
 from paper_1705_02313_gb300 import gen
 
 import certificate as cert
@@ -48,6 +50,13 @@ def game():
     return g, gp
 
 
+@pytest.fixture(scope="module")
+def game_cv():
+    g = gen.native_random_game(N, DMIN, DMAX, SEED, levels=4)
+    gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+    return g, gp
+
+
 def gpu_solve(pg, ctx, g, max_inner=0):
     """pg_load_csr from device arrays, pg_solve into device arrays; returns
     host copies, the status and the iteration counts."""
@@ -56,6 +65,7 @@ def gpu_solve(pg, ctx, g, max_inner=0):
     game = pg.pg_load_csr(ctx, g.n, g.m, *d)
     try:
         _, _, k = pg.pg_game_info(game)
+        nlev = pg.pg_game_levels(game).size
         dev = dict(win=torch.empty(g.n, dtype=torch.uint8, device="cuda"),
                    sigma=torch.empty(g.n, dtype=torch.int32, device="cuda"),
                    tau=torch.empty(g.n, dtype=torch.int32, device="cuda"),
@@ -63,6 +73,8 @@ def gpu_solve(pg, ctx, g, max_inner=0):
                    val_depth=torch.empty(g.n, dtype=torch.int32, device="cuda"),
                    val_rank=torch.empty(g.n, dtype=torch.int32, device="cuda"),
                    dummy_sigma=torch.empty(max(k, 1), dtype=torch.int8, device="cuda"))
+        if nlev:
+            dev["val_counts"] = torch.empty(g.n * nlev, dtype=torch.int32, device="cuda")
         try:
             major, inner = pg.pg_solve(ctx, game, max_inner=max_inner, **dev)
             rc = pg.PG_OK
@@ -72,6 +84,8 @@ def gpu_solve(pg, ctx, g, max_inner=0):
         torch.cuda.synchronize()
         out = {key: t.cpu().numpy() for key, t in dev.items()}
         out["dummy_sigma"] = out["dummy_sigma"][:k]
+        if nlev:
+            out["val_counts"] = out["val_counts"].reshape(g.n, nlev)
     finally:
         pg.pg_game_free(game)
     return rc, major, inner, used, iters, out
@@ -105,3 +119,24 @@ def test_full_size_solution_certified(pg, ctx, game):
     assert rc == pg.PG_OK and used and iters == inner and major > 0
     cert.certify(gp, g.offsets, g.targets, got)
     assert 0 < int(got["win"].sum()) < g.n  # both players win somewhere
+
+
+def test_full_size_count_vectors_first_valuations(pg, ctx, game_cv):
+    g, gp = game_cv
+    rc, _, _, used, iters, got = gpu_solve(pg, ctx, g, max_inner=3)
+    assert rc == pg.PG_ETIMEOUT and used and iters == 3
+    r = o3.run(gp, max_inner=3, allow_timeout=True)
+    assert r["status"] == o3.ETIMEOUT and r["inner"] == 3
+    sigma, tau, dsig = profile_to_original(gp, r["strat"])
+    assert_equal(got, dict(sigma=sigma, tau=tau, dummy_sigma=dsig), ["sigma", "tau", "dummy_sigma"], "profile")
+    val = o3.valuate(gp, r["strat"])
+    want = o3.map_back(gp, dict(val, strat=r["strat"]))
+    assert_equal(got, want, ["win", "val_class", "val_depth", "val_counts"], "valuation")
+    assert (got["val_rank"] == -1).all()
+
+
+def test_full_size_count_vectors_certified(pg, ctx, game_cv):
+    g, gp = game_cv
+    rc, major, inner, used, iters, got = gpu_solve(pg, ctx, g)
+    assert rc == pg.PG_OK and used and iters == inner and major > 0
+    cert.certify_counts(gp, g.offsets, g.targets, got)
