@@ -377,6 +377,16 @@ pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
  * valuations it computed (each may be NULL). */
 pg_status pg_last_loop(const pg_game *game, int32_t *graph, int64_t *iterations);
 
+/* Device memory of games (loads, scratch, batches, servers) comes from one
+ * stream-ordered pool per device. Freed game memory stays cached in the pool,
+ * up to a quarter of the device's memory, so that loading the next game
+ * reuses it instead of mapping new memory. This call waits for the device and
+ * returns everything the pool caches on `device` to the driver (for example
+ * before other code in the process allocates large buffers); memory of live
+ * games is untouched. PG_ECUDA if the device cannot be used. The paper has no
+ * counterpart (memory management of the implementation only). */
+pg_status pg_release_cached_memory(int device);
+
 #ifdef __cplusplus
 }
 #endif

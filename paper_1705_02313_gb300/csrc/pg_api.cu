@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include "pg_internal.cuh"
 
 namespace pg {
@@ -30,6 +32,55 @@ void drop_loop_graphs(pg_game* g) {
     }
 }
 
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+
+cudaError_t game_pool(int device, cudaMemPool_t* out) {
+    if (device < 0 || device >= kPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        size_t free_b = 0, total_b = 0;
+        e = cudaMemGetInfo(&free_b, &total_b);
+        uint64_t keep = e == cudaSuccess ? (uint64_t)total_b / 4 : 0;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pool[device] = p;
+    }
+    *out = g_pool[device];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t dev_alloc(pg_ctx* ctx, void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = game_pool(ctx->device, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
+}
+
+cudaError_t dev_trim(int device) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = game_pool(device, &pool);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? cudaMemPoolTrimTo(pool, 0) : e;
+}
+
+// Work of any stream may still read the game (batch loaders, the server's
+// worker): the device is synchronised once, as cudaFree would, and then every
+// buffer goes back to the pool.
 void free_game(pg_game* g) {
     if (!g) return;
     void* ptrs[] = {g->off,  g->off64,   g->vgame, g->gsink, g->gst,   g->gactive, g->gscan,
@@ -37,8 +88,9 @@ void free_game(pg_game* g) {
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
                     g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
+    cudaDeviceSynchronize();
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);
     if (g->hcnt) cudaFreeHost(g->hcnt);
     for (auto& x : g->loop_exec)
         if (x) cudaGraphExecDestroy(x);
@@ -176,7 +228,7 @@ pg_status write_outputs(pg_game* g, int32_t mem_kind, uint8_t* win, int32_t* sig
     OutPtrs o = {g->cv ? 1 : 0, win, sigma, tau, vclass, vdepth, vrank, vdom, dsig};
     Stage L = stage_layout(g->n0, g->k);
     if (mem_kind == PG_MEM_HOST) {
-        if (!g->stage) PG_CUDA_TRY(ctx, cudaMalloc(&g->stage, L.bytes));
+        if (!g->stage) PG_CUDA_TRY(ctx, dev_alloc(ctx, &g->stage, L.bytes, s));
         char* b = (char*)g->stage;
         o = {g->cv ? 1 : 0,
              win ? (uint8_t*)(b + L.off_win) : nullptr,     sigma ? (int32_t*)(b + L.off_sigma) : nullptr,
@@ -219,25 +271,26 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
     const int32_t *ds = sigma, *dt = tau;
     const int8_t* dd = dsig;
     int32_t* buf = nullptr;
+    cudaError_t e = cudaSuccess;
     if (mem_kind == PG_MEM_HOST && (sigma || tau || dsig)) {
         size_t bytes = 8 * (size_t)g->n0 + (size_t)g->k + 16;
-        PG_CUDA_TRY(ctx, cudaMalloc(&buf, bytes));
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&buf, bytes, s));
         char* b = (char*)buf;
         if (sigma) {
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b, sigma, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s));
+            e = cudaMemcpyAsync(b, sigma, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s);
             ds = (const int32_t*)b;
         }
-        if (tau) {
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b + 4 * (size_t)g->n0, tau, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s));
+        if (tau && e == cudaSuccess) {
+            e = cudaMemcpyAsync(b + 4 * (size_t)g->n0, tau, 4 * (size_t)g->n0, cudaMemcpyHostToDevice, s);
             dt = (const int32_t*)(b + 4 * (size_t)g->n0);
         }
-        if (dsig && g->k) {
-            PG_CUDA_TRY(ctx, cudaMemcpyAsync(b + 8 * (size_t)g->n0, dsig, (size_t)g->k, cudaMemcpyHostToDevice, s));
+        if (dsig && g->k && e == cudaSuccess) {
+            e = cudaMemcpyAsync(b + 8 * (size_t)g->n0, dsig, (size_t)g->k, cudaMemcpyHostToDevice, s);
             dd = (const int8_t*)(b + 8 * (size_t)g->n0);
         }
     }
     int32_t* err = &g->cnt->err;
-    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) {
         ctx->launches += 1;
         if (g->off64)
@@ -251,7 +304,7 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
         e = cudaMemcpyAsync(ctx->pinned, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (buf) cudaFree(buf);
+    if (buf) cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_profile");
     if (ctx->pinned[0]) return fail(ctx, PG_EINVAL, "profile names a successor that is not an edge of its vertex");
     return PG_OK;
@@ -442,6 +495,16 @@ pg_status pg_set_stream(pg_ctx* ctx, void* stream) {
 }
 
 const char* pg_last_error(const pg_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+pg_status pg_release_cached_memory(int device) {
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return PG_ECUDA;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return PG_ECUDA;
+    cudaError_t e = dev_trim(device);
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? PG_OK : PG_ECUDA;
+}
 
 pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;

@@ -585,10 +585,11 @@ pg_status bellman_ford_cv(pg_game* g, int64_t* rounds) {
 pg_status alloc_cv(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     const int64_t n = g->n;
-    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->ws, sizeof(i128) * n));
-    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->wsB, sizeof(i128) * n));
-    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->gdB, sizeof(uint64_t) * n));
-    PG_CUDA_TRY(ctx, cudaMalloc((void**)&g->key128, sizeof(i128) * n));
+    cudaStream_t s = ctx->stream;
+    PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->ws, sizeof(i128) * n, s));
+    PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->wsB, sizeof(i128) * n, s));
+    PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->gdB, sizeof(uint64_t) * n, s));
+    PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->key128, sizeof(i128) * n, s));
     return PG_OK;
 }
 

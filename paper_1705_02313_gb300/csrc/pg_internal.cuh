@@ -289,6 +289,13 @@ pg_status enqueue_reset(pg_game* g);
 // Resets the per-game state for a new solve.
 pg_status reset_games(pg_game* g);
 void free_game(pg_game* g);
+// Device memory of games: stream-ordered allocations from one pool per
+// device that keeps freed memory cached (up to a quarter of the device's
+// memory) for the next game, instead of mapping and unmapping it each time.
+// Everything free_game releases comes from here.
+cudaError_t dev_alloc(pg_ctx* ctx, void** p, size_t bytes, cudaStream_t s);
+// Returns the pool's cached memory to the device (pg_release_cached_memory).
+cudaError_t dev_trim(int device);
 // Co-resident blocks of the cooperative valuation kernels on a device.
 pg_status coop_blocks_for(pg_ctx* ctx, int* out);
 pg_status chain1_blocks_for(pg_ctx* ctx, int* out);

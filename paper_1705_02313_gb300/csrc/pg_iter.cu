@@ -1093,7 +1093,7 @@ void prof_collect(pg_game* g) {
 pg_status alloc_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     const int64_t n = g->n;
-    auto A = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 1); };
+    auto A = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes, ctx->stream); };
     PG_CUDA_TRY(ctx, A((void**)&g->gd, sizeof(uint64_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->gd32, sizeof(uint32_t) * n));
     PG_CUDA_TRY(ctx, A((void**)&g->kind, n));

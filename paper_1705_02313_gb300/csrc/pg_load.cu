@@ -217,27 +217,29 @@ __global__ void k_maps(int32_t n0, int32_t k, const int32_t* nid, int32_t* nid0,
     }
 }
 
-// The game's own arrays, stream-ordered on the load stream (no global
-// allocation lock between concurrent loads); the load synchronises its
-// stream before returning, so they are valid on every stream afterwards.
+// The game's own arrays, stream-ordered on the load stream from the game
+// pool (no global allocation lock between concurrent loads); the load
+// synchronises its stream before returning, so they are valid on every stream
+// afterwards.
 template <typename T>
-cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
-    return cudaMallocAsync((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
+cudaError_t dalloc(pg_ctx* ctx, T** p, int64_t count, cudaStream_t s) {
+    return dev_alloc(ctx, (void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
 }
 
 // Temporaries of one load, stream-ordered on the load's stream (allocating
 // and freeing them does not synchronise the device, so loads can overlap
 // other streams' work).
 struct Temps {
+    pg_ctx* ctx;
     cudaStream_t s;
     std::vector<void*> ptrs;
-    explicit Temps(cudaStream_t st) : s(st) {}
+    Temps(pg_ctx* c, cudaStream_t st) : ctx(c), s(st) {}
     ~Temps() {
         for (void* p : ptrs) cudaFreeAsync(p, s);
     }
     template <typename T>
     cudaError_t get(T** p, int64_t count) {
-        cudaError_t e = cudaMallocAsync((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
+        cudaError_t e = dev_alloc(ctx, (void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
         if (e == cudaSuccess) ptrs.push_back((void*)*p);
         return e;
     }
@@ -255,7 +257,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     if (m < n || m > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: m must be in [n, 2^31-1)");
     cudaStream_t s = ctx->stream;
     cudaMemcpyKind kind = mem_kind == PG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    Temps T(s);
+    Temps T(ctx, s);
     int32_t *off, *tgt, *pri;
     uint8_t* own;
     LoadScalars* sc;
@@ -375,16 +377,16 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         cudaError_t _e = (expr);                      \
         if (_e != cudaSuccess) return bail(_e, #expr); \
     } while (0)
-    LG_TRY(dalloc(&g->off, np + 2, s));
-    LG_TRY(dalloc(&g->tgt, mp, s));
-    LG_TRY(dalloc(&g->flags, np + 1, s));
-    LG_TRY(dalloc(&g->pri, np + 1, s));
-    LG_TRY(dalloc(&g->nid0, n, s));
-    LG_TRY(dalloc(&g->orig_of, np + 1, s));
-    LG_TRY(dalloc(&g->dnid, k, s));
-    LG_TRY(dalloc(&g->dummy_of, k, s));
-    LG_TRY(dalloc(&g->strat, np + 1, s));
-    LG_TRY(dalloc(&g->gsink, 1, s));
+    LG_TRY(dalloc(ctx, &g->off, np + 2, s));
+    LG_TRY(dalloc(ctx, &g->tgt, mp, s));
+    LG_TRY(dalloc(ctx, &g->flags, np + 1, s));
+    LG_TRY(dalloc(ctx, &g->pri, np + 1, s));
+    LG_TRY(dalloc(ctx, &g->nid0, n, s));
+    LG_TRY(dalloc(ctx, &g->orig_of, np + 1, s));
+    LG_TRY(dalloc(ctx, &g->dnid, k, s));
+    LG_TRY(dalloc(ctx, &g->dummy_of, k, s));
+    LG_TRY(dalloc(ctx, &g->strat, np + 1, s));
+    LG_TRY(dalloc(ctx, &g->gsink, 1, s));
     ++ctx->launches;
     k_dummy_of<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, g->dummy_of);
 

@@ -153,7 +153,7 @@ pg_status alloc_batch(pg_server* sv) {
     g->n = (int32_t)sv->capN;
     g->m = sv->capM;
     sv->B = g;
-    auto A = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 1); };
+    auto A = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes, ctx->stream); };
     const int64_t N = sv->capN, M = sv->capM;
     if (M > INT32_MAX - 1) PG_CUDA_TRY(ctx, A((void**)&g->off64, sizeof(int64_t) * (N + 1)));
     else PG_CUDA_TRY(ctx, A((void**)&g->off, sizeof(int32_t) * (N + 1)));

@@ -286,3 +286,25 @@ def test_errors(pg, ctx):
         assert e.value.code == pg.PG_ENOTADMISSIBLE
     finally:
         pg.pg_game_free(game)
+
+
+def test_memory_pool_reuse_and_release(pg, ctx):
+    # freed game memory stays cached in the pool and is reused by the next
+    # load; releasing it hands it back to the device; results do not change
+    import torch
+    g = gen.random_game(200_000, 2, 5, 3)
+    first = pg.solve_arrays(ctx, g.n, *g.arrays())
+    for _ in range(2):
+        again = pg.solve_arrays(ctx, g.n, *g.arrays())
+        for k in KEYS:
+            assert np.array_equal(first[k], again[k]), k
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    pg.pg_release_cached_memory(0)
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after - free_before >= 16 << 20  # at least the game's own arrays were cached
+    again = pg.solve_arrays(ctx, g.n, *g.arrays())
+    for k in KEYS:
+        assert np.array_equal(first[k], again[k]), k
+    with pytest.raises(pg.PgError):
+        pg.pg_release_cached_memory(-1)
