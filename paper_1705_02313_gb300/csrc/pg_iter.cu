@@ -279,24 +279,61 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
     }
 }
 
+// Size additions near the roots of deep g-trees. Every vertex of a large
+// g-tree has the same few vertices near the root among its ancestors, and one
+// global atomic per vertex on each of them would serialise (an n-long chain: n
+// additions on one word). Chains of at least kDeepChain vertices therefore add
+// their top kHotTop ancestors into a per-block table in shared memory (open
+// addressing, kHotProbes probes, then the global atomic), flushed once per
+// block. Shorter chains (most vertices of random games) add directly: in the
+// table they would only crowd out the hot entries. The launch bound keeps five
+// blocks per SM.
+constexpr int kHotSlots = 2048;
+constexpr int kHotBits = 11;
+constexpr int kHotProbes = 4;
+constexpr int kHotTop = 8;
+constexpr int kDeepChain = 4;
+
+__device__ inline void hot_add(int32_t x, int32_t* tkey, int32_t* tcnt, int32_t* sz) {
+    const uint32_t h = ((uint32_t)x * 2654435761u) >> (32 - kHotBits);
+#pragma unroll
+    for (int p = 0; p < kHotProbes; ++p) {
+        const uint32_t i = (h + p) & (kHotSlots - 1);
+        int32_t k = *(volatile int32_t*)&tkey[i];
+        if (k == -1) k = atomicCAS(&tkey[i], -1, x);
+        if (k == -1 || k == x) {
+            atomicAdd(&tcnt[i], 1);
+            return;
+        }
+    }
+    atomicAdd(sz + x, 1);
+}
+
 // Classification and g-subtree sizes. Each vertex walks its g-chain (4-byte
 // words) to its end: the sink means a finite valuation, a "none" vertex
 // means TOP (odd cycle if that cycle maximum is odd). Finite vertices then
 // take a slot among their g-parent's children and add one to each g-ancestor
-// below the sink. TOP vertices touch nothing else, so large TOP components
-// cause no atomic hot spots.
-__global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __restrict__ gd32,
+// below the sink (the top ones of deep chains through the block's table).
+// TOP vertices touch nothing else, so large TOP components cause no atomic hot
+// spots.
+__global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t* __restrict__ gd32,
                                                    const uint8_t* __restrict__ flags, const int32_t* __restrict__ pri,
                                                    int32_t* sz, int32_t* ccnt, int32_t* __restrict__ slot,
                                                    uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
                                                    int32_t* __restrict__ dom, int want_dom,
                                                    const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt) {
+    __shared__ int32_t tkey[kHotSlots], tcnt[kHotSlots];
+    for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
+        tkey[i] = -1;
+        tcnt[i] = 0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t nfin = 0, nodd = 0;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
          tile += nwarps) {
-        int32_t v[kIlp], g[kIlp], x[kIlp], cyc[kIlp];
+        int32_t v[kIlp], g[kIlp], x[kIlp], cyc[kIlp], len[kIlp];
         bool act[kIlp], sinkchild[kIlp], slotid[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
@@ -307,9 +344,10 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
             sinkchild[j] = g32_sink(w);
             cyc[j] = g32_none(w) ? g[j] : -1;
             x[j] = g[j];
+            len[j] = 0;
             act[j] = v[j] < n && !slotid[j] && !g32_none(w) && !sinkchild[j];
         }
-        // classification walks
+        // classification walks (len: the vertices from g(v) to the chain's end)
         for (;;) {
             bool any = false;
             uint32_t wx[kIlp];
@@ -318,6 +356,7 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
                 if (act[j]) {
+                    ++len[j];
                     if (g32_none(wx[j])) {
                         cyc[j] = g32_ptr(wx[j]);
                         act[j] = false;
@@ -332,18 +371,24 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
         }
         // finite vertices below a vertex parent: slot, then sizes along the chain
         int32_t sl[kIlp];
+        bool deep[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             act[j] = v[j] < n && !slotid[j] && cyc[j] < 0 && !sinkchild[j];
             sl[j] = act[j] ? atomicAdd(ccnt + g[j], 1) : -1;
             x[j] = g[j];
+            deep[j] = len[j] >= kDeepChain;
         }
         for (;;) {
             bool any = false;
             uint32_t wx[kIlp];
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
-                if (act[j]) atomicAdd(sz + x[j], 1);
+                if (act[j]) {  // len[j]: the additions still to come on this chain, this one included
+                    if (deep[j] && len[j] <= kHotTop) hot_add(x[j], tkey, tcnt, sz);
+                    else atomicAdd(sz + x[j], 1);
+                    --len[j];
+                }
                 wx[j] = act[j] ? gd32[x[j]] : 0u;
             }
 #pragma unroll
@@ -382,6 +427,9 @@ __global__ void __launch_bounds__(kBlock) k_chain1(int32_t n, const uint32_t* __
             slot[v[j]] = sl[j];
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x)
+        if (tcnt[i]) atomicAdd(sz + tkey[i], tcnt[i]);
     block_add(nfin, &cnt->n_fin);
     block_add(nodd, &cnt->n_odd);
 }
