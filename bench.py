@@ -298,40 +298,52 @@ def batch_measure(name, cpu_budget=0):
     """Solves the batch three ways, each once after a warm-up on its first
     games: pg_solve_batch with the inputs already in device memory, the same
     from host arrays with results copied back (end to end), and a loop of
-    pg_load_csr + pg_solve over the same games one at a time."""
+    pg_load_csr + pg_solve over the same games one at a time. With several
+    ranks every rank takes its share of the games (largest first to the
+    least loaded rank) and solves it alone; throughput is all games over the
+    slowest rank's time."""
     import torch
 
-    from paper_1705_02313_gb300 import gen, pg
+    from paper_1705_02313_gb300 import gen, pg, shard
+    ws, rank, _ = dist_env()
     count, lo, hi, dmin, dmax, desc = BATCHES[name]
+    sizes_all = gen.log_uniform_sizes(count, lo, hi).astype(np.int64)
+    mine = shard.shard_of(sizes_all, ws, rank) if ws > 1 else None
     t0 = time.perf_counter()
-    vb, eb, off, tgt, own, pri = gen.native_batch(count, lo, hi, dmin, dmax)
+    vb, eb, off, tgt, own, pri = gen.native_batch(count, lo, hi, dmin, dmax, indices=mine)
     t_gen = time.perf_counter() - t0
+    local = count if mine is None else int(mine.size)
     n0, m0 = int(vb[-1]), int(eb[-1])
     dev = [torch.from_numpy(a).cuda() for a in (off, tgt, own, pri)]
-    out = dict(win=torch.empty(n0, dtype=torch.uint8, device="cuda"),
-               sigma=torch.empty(n0, dtype=torch.int32, device="cuda"))
-    ctx = pg.pg_ctx_create(0)
+    out = dict(win=torch.empty(max(n0, 1), dtype=torch.uint8, device="cuda"),
+               sigma=torch.empty(max(n0, 1), dtype=torch.int32, device="cuda"))
+    ctx = pg.pg_ctx_create(torch.cuda.current_device())
     try:
-        w = min(count, 16)  # warm-up: the first games
-        pg.pg_solve_batch(ctx, w, vb[:w + 1], eb[:w + 1], *dev, **out)
+        w = min(local, 16)  # warm-up: the first games
+        if w:
+            pg.pg_solve_batch(ctx, w, vb[:w + 1], eb[:w + 1], *dev, **out)
         torch.cuda.synchronize()
+        shard.barrier()
         t0 = time.perf_counter()
-        res = pg.pg_solve_batch(ctx, count, vb, eb, *dev, **out)
+        res = pg.pg_solve_batch(ctx, local, vb, eb, *dev, **out) if local else None
         torch.cuda.synchronize()
-        t_batch = time.perf_counter() - t0
-        win_b = out["win"].cpu().numpy()
-        sig_b = out["sigma"].cpu().numpy()
+        t_batch = shard.max_over_ranks(time.perf_counter() - t0)
+        win_b = out["win"].cpu().numpy()[:n0]
+        sig_b = out["sigma"].cpu().numpy()[:n0]
         # end to end: host inputs, results back in host memory
         hwin = np.empty(n0, np.uint8)
         hsig = np.empty(n0, np.int32)
+        shard.barrier()
         t0 = time.perf_counter()
-        pg.pg_solve_batch(ctx, count, vb, eb, off, tgt, own, pri, win=hwin, sigma=hsig)
-        t_e2e = time.perf_counter() - t0
+        if local:
+            pg.pg_solve_batch(ctx, local, vb, eb, off, tgt, own, pri, win=hwin, sigma=hsig)
+        t_e2e = shard.max_over_ranks(time.perf_counter() - t0)
         # one game at a time through the single-game entry points
         o_off, o_tgt, o_own, o_pri = dev
+        shard.barrier()
         t0 = time.perf_counter()
         inner_sum = 0
-        for i in range(count):
+        for i in range(local):
             a, b = int(vb[i]), int(vb[i + 1])
             e0, e1 = int(eb[i]), int(eb[i + 1])
             g = pg.pg_load_csr(ctx, b - a, e1 - e0, o_off[a + i:b + i + 1], o_tgt[e0:e1], o_own[a:b], o_pri[a:b])
@@ -341,32 +353,43 @@ def batch_measure(name, cpu_budget=0):
             finally:
                 pg.pg_game_free(g)
         torch.cuda.synchronize()
-        t_single = time.perf_counter() - t0
-        same = bool(np.array_equal(win_b, out["win"].cpu().numpy()) and np.array_equal(sig_b, out["sigma"].cpu().numpy())
-                    and np.array_equal(win_b, hwin) and np.array_equal(sig_b, hsig))
+        t_single = shard.max_over_ranks(time.perf_counter() - t0)
+        same = bool(np.array_equal(win_b, out["win"].cpu().numpy()[:n0]) and
+                    np.array_equal(sig_b, out["sigma"].cpu().numpy()[:n0]) and
+                    np.array_equal(win_b, hwin) and np.array_equal(sig_b, hsig))
     finally:
         pg.pg_ctx_destroy(ctx)
-    inner = res["inner"]
+    same = all(shard.gather_to_all(same))
+    inner_sum = int(shard.sum_over_ranks(inner_sum))
+    its = int(shard.max_over_ranks(res["iterations"] if res else 0))
+    inner_lo = int(-shard.max_over_ranks(-(int(res["inner"].min()) if res else 10**9)))
+    inner_hi = int(shard.max_over_ranks(int(res["inner"].max()) if res else 0))
     cpu = None
-    if cpu_budget > 0:
+    if cpu_budget > 0 and rank == 0:
         c = cpu_batch(count, lo, hi, dmin, dmax, cpu_budget)
         k = c["games"]
-        oracle_same = all(np.array_equal(c["win"][i], win_b[vb[i]:vb[i + 1]]) and
-                          np.array_equal(c["sigma"][i], sig_b[vb[i]:vb[i + 1]]) for i in range(k))
+        if mine is None:
+            oracle_same = all(np.array_equal(c["win"][i], win_b[vb[i]:vb[i + 1]]) and
+                              np.array_equal(c["sigma"][i], sig_b[vb[i]:vb[i + 1]]) for i in range(k))
+        else:
+            oracle_same = None  # the games of the sample are spread over the ranks
         cpu = {"value": k / c["seconds"], "unit": "games/s", "cores": c["cores"], "kind": "oracle",
                "sample": "games 0..%d of the batch (%d vertices), one game per process on %d processes, %.1f s wall "
                          "(%.1f s of single-thread solves); each worker generates its game before timing the solve"
                          % (k - 1, c["vertices"], c["cores"], c["seconds"], c["solve_seconds"]),
-               "identical_to_gpu": bool(oracle_same)}
-    return {"workload": name, "description": desc, "games": count, "vertices": n0, "edges": m0,
+               "identical_to_gpu": oracle_same}
+    return {"workload": name, "description": desc, "games": count, "vertices": int(sizes_all.sum()),
+            "edges": int(shard.sum_over_ranks(m0)), "ranks": ws,
+            "games_per_rank": [int(x) for x in shard.gather_to_all(local)],
             "metric": "batched games/s vs one-at-a-time", "unit": "games/s",
             "batched_games_per_s": count / t_batch, "batched_e2e_games_per_s": count / t_e2e,
             "one_at_a_time_games_per_s": count / t_single, "speedup": t_single / t_batch,
             "batched_s": t_batch, "batched_e2e_s": t_e2e, "one_at_a_time_s": t_single,
-            "lockstep_iterations": int(res["iterations"]), "inner_min": int(inner.min()),
-            "inner_max": int(inner.max()), "valuations_one_at_a_time": int(inner_sum),
+            "lockstep_iterations": its, "inner_min": inner_lo,
+            "inner_max": inner_hi, "valuations_one_at_a_time": inner_sum,
             "generate_s": t_gen, "identical_results": same, "cpu_baseline": cpu,
-            "timing": "wall clock around each call, device synchronised; includes loading and preprocessing"}
+            "timing": "wall clock around each call, device synchronised; includes loading and preprocessing; "
+                      "with several ranks, the slowest rank's time"}
 
 
 # ---------------------------------------------------------------------------
@@ -708,8 +731,10 @@ def run_ours(args):
         line["count_vector"] = cv_measure(args.cv_workload, ctx)
     if rank == 0 and args.chain > 0:
         line["long_chain"] = chain_measure(args.chain, ctx)
-    if rank == 0 and not args.no_batch:
-        line["batch"] = batch_measure(args.batch, 0 if args.no_cpu_baseline else args.batch_cpu_vertices)
+    if not args.no_batch:  # every rank solves its share of the batch's games
+        b = batch_measure(args.batch, 0 if args.no_cpu_baseline else args.batch_cpu_vertices)
+        if rank == 0:
+            line["batch"] = b
     if rank == 0 and args.serve > 0:
         line["serve"] = serve_measure("serve-200", args.serve, 0 if args.no_cpu_baseline else args.serve_cpu_vertices)
     if rank == 0 and not args.no_cpu_baseline:

@@ -287,14 +287,19 @@ def native_random_game(n, dmin, dmax, seed=0, p_odd=0.5, nthreads=0, levels=0):
     return Game(n, off, tgt, own, pri)
 
 
-def native_batch(count, lo, hi, dmin, dmax, p_odd=0.5, seed=0, nthreads=0, alloc=None):
+def native_batch(count, lo, hi, dmin, dmax, p_odd=0.5, seed=0, nthreads=0, alloc=None, indices=None):
     """The batch of batch_games(count, lo, hi, dmin, dmax, p_odd, seed), packed
     in the pg_solve_batch layout. ``alloc(shape_len, numpy_dtype)`` may supply
     the four data buffers (for example pinned host tensors); by default numpy
-    arrays are used. Returns (vtx_base, edge_base, offsets, targets, owner, pri)."""
+    arrays are used. ``indices`` (optional) packs only those games of the
+    batch, in that order (one rank's share). Returns (vtx_base, edge_base,
+    offsets, targets, owner, pri)."""
     lib = _gen_lib()
     sizes = log_uniform_sizes(count, lo, hi, seed).astype(np.int64)
-    seeds = np.array([batch_seed(i) for i in range(count)], np.uint64)
+    ids = np.arange(count, dtype=np.int64) if indices is None else np.asarray(indices, dtype=np.int64)
+    sizes = np.ascontiguousarray(sizes[ids])
+    count = int(ids.size)
+    seeds = np.array([batch_seed(int(i)) for i in ids], np.uint64)
     seeds_p = seeds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
     ecount = np.zeros(count, np.int64)
     nt = _threads(nthreads)
