@@ -126,7 +126,8 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# per-kernel algorithmic bytes (the compulsory traffic of each pass)
+# per-kernel algorithmic bytes: the compulsory traffic of each pass (each per-id array once at its element size,
+# one gather per edge)
 
 def algorithmic_bytes(name, s):
     """Compulsory bytes of one launch of a kernel class: every per-id array
