@@ -163,11 +163,23 @@ def kernel_entry(name, v, s, hbm):
     return e
 
 
-def kernel_source_hash():
+# the source file of each kernel class whose DRAM traffic is recorded
+KERNEL_SOURCE = {"chain1": "pg_iter.cu", "walk": "pg_iter.cu", "chain2": "pg_iter.cu", "scatter": "pg_iter.cu",
+                 "siblings": "pg_iter.cu", "switch_odd": "pg_iter.cu"}
+
+
+def kernel_source_hash(kernel="chain1"):
+    """Hash of what the kernel is compiled from: its source file and the
+    compile-time constants of the internal header (host-side structures
+    elsewhere do not change the kernel)."""
+    csrc = os.path.join(ROOT, "paper_1705_02313_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1705_02313_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1705_02313_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, KERNEL_SOURCE.get(kernel, "pg_iter.cu")), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "pg_internal.cuh"), "rb") as fh:
+        for line in fh.read().splitlines():
+            if line.strip().startswith(b"constexpr"):
+                h.update(line + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -179,7 +191,7 @@ def measured_traffic(kernel, workload):
         with open(path) as f:
             t = json.load(f)
         e = t[workload][kernel]
-        if e.get("source_hash") != kernel_source_hash():
+        if e.get("source_hash") != kernel_source_hash(kernel):
             return None
         return e["dram_bytes_per_launch"]
     except Exception:

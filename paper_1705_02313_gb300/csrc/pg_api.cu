@@ -48,9 +48,9 @@ cudaError_t game_pool(int device, cudaMemPool_t* out) {
         cudaMemPool_t p = nullptr;
         cudaError_t e = cudaMemPoolCreate(&p, &props);
         if (e != cudaSuccess) return e;
-        size_t free_b = 0, total_b = 0;
-        e = cudaMemGetInfo(&free_b, &total_b);
-        uint64_t keep = e == cudaSuccess ? (uint64_t)total_b / 4 : 0;
+        cudaDeviceProp prop;
+        e = cudaGetDeviceProperties(&prop, device);
+        uint64_t keep = e == cudaSuccess ? (uint64_t)prop.totalGlobalMem / 4 : 0;
         e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
         if (e != cudaSuccess) {
             cudaMemPoolDestroy(p);
@@ -88,6 +88,9 @@ void free_game(pg_game* g) {
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
                     g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
+    int prev = -1;
+    const bool switched =
+        cudaGetDevice(&prev) == cudaSuccess && prev != g->device && cudaSetDevice(g->device) == cudaSuccess;
     cudaDeviceSynchronize();
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);
@@ -98,6 +101,7 @@ void free_game(pg_game* g) {
         if (e) cudaEventDestroy(e);
     for (auto& e : g->kev)
         if (e) cudaEventDestroy(e);
+    if (switched) cudaSetDevice(prev);
     delete g;
 }
 

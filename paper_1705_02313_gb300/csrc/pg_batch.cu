@@ -74,6 +74,7 @@ pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out
     if (K > INT32_MAX) return fail(ctx, PG_EUNSUPPORTED, "pg_solve_batch: too many dummy vertices");
     pg_game* g = new pg_game();
     g->ctx = ctx;
+    g->device = ctx->device;
     g->ngames = ngames;
     g->n = (int32_t)N;
     g->m = M;

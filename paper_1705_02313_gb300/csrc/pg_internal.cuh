@@ -156,6 +156,7 @@ struct Levels {
 // game, as the nearest-greater walks need). A single game is a batch of one.
 struct pg_game {
     pg_ctx* ctx = nullptr;
+    int device = 0;   // the device holding the game's memory
     int32_t ngames = 1;
     int64_t n0 = 0;   // original vertices, all games
     int64_t m0 = 0;   // original edges, all games

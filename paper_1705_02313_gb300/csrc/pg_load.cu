@@ -359,6 +359,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
 
     pg_game* g = new pg_game();
     g->ctx = ctx;
+    g->device = ctx->device;
     g->n0 = n;
     g->m0 = m;
     g->k = k;

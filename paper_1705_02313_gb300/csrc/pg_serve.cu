@@ -149,6 +149,7 @@ pg_status alloc_batch(pg_server* sv) {
     pg_ctx* ctx = sv->ctx;
     pg_game* g = new pg_game();
     g->ctx = ctx;
+    g->device = ctx->device;
     g->ngames = sv->capG;
     g->n = (int32_t)sv->capN;
     g->m = sv->capM;
