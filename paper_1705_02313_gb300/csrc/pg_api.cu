@@ -87,7 +87,7 @@ void free_game(pg_game* g) {
                     g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
-                    g->tiles, g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
+                    g->tiles, g->tsum,   g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
     int prev = -1;
     const bool switched =
         cudaGetDevice(&prev) == cudaSuccess && prev != g->device && cudaSetDevice(g->device) == cudaSuccess;

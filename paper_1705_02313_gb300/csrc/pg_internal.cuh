@@ -209,6 +209,7 @@ struct pg_game {
     int32_t* dom = nullptr;      // [n] dominant priority of the cycle reached (TOP), -1 finite
     int32_t* hugelist = nullptr; // [n] parents with more than kHugeChildren children
     int64_t* tiles = nullptr;    // [2 * ntiles + 2] id-ordered scan tile sums
+    int64_t* tsum = nullptr;     // [2 * ntiles + 2] (even, odd) sizes of the sink's children per tile, summed by k_scatter
     int64_t ntiles = 0;
     int64_t* gscan = nullptr;    // [3 * ngames] per game: even and odd prefix at its first id, odd prefix at its sink
     pg::Counters* cnt = nullptr; // device counters

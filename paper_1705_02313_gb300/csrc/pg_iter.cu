@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* _
                                                     const uint8_t* __restrict__ kind, const int32_t* __restrict__ sz,
                                                     const int32_t* __restrict__ coff, const int32_t* __restrict__ slot,
                                                     int32_t* __restrict__ ccnt, int2* __restrict__ cl_ks,
-                                                    int32_t* __restrict__ sinkval) {
+                                                    int32_t* __restrict__ sinkval, int64_t* __restrict__ tsum) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -463,15 +463,31 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* _
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) base[j] = ent[j] ? coff[base[j]] : 0;
+        int32_t se = 0, so = 0;  // sizes of the sink's children in this warp tile (disjoint subtrees: < 2^31)
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             if (v[j] >= n) continue;
             const bool odd = (kd[j] & kKOdd) != 0;
             ccnt[v[j]] = 0;
             int32_t sv = 0;
-            if ((kd[j] & kKFin) && (kd[j] & kKSinkChild)) sv = s[j] | (odd ? INT32_MIN : 0);
+            if ((kd[j] & kKFin) && (kd[j] & kKSinkChild)) {
+                sv = s[j] | (odd ? INT32_MIN : 0);
+                if (odd) so += s[j];
+                else se += s[j];
+            }
             if (ent[j]) cl_ks[base[j] + sl[j]] = make_int2(order_key(v[j], odd), s[j]);
             sinkval[v[j]] = sv;
+        }
+        // the tile sums of the id-ordered scan over the sink's children (a warp tile lies in one scan tile)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            se += __shfl_down_sync(kFull, se, o);
+            so += __shfl_down_sync(kFull, so, o);
+        }
+        if (lane == 0) {
+            const int64_t t = warp_tile_base(tile) / kCoopTile;
+            if (se) atomicAdd((unsigned long long*)&tsum[2 * t], (unsigned long long)se);
+            if (so) atomicAdd((unsigned long long*)&tsum[2 * t + 1], (unsigned long long)so);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ccnt[n] = 0;
@@ -683,36 +699,27 @@ __device__ inline void load8(const int32_t* __restrict__ sinkval, int32_t n, int
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_sink_reduce(int32_t n, const int32_t* __restrict__ sinkval, int64_t* tiles) {
-    const int64_t i0 = (int64_t)blockIdx.x * kCoopTile + (int64_t)threadIdx.x * kCIpt;
-    int32_t v[kCIpt];
-    load8(sinkval, n, i0, v);
-    int32_t e = 0, o = 0;
-#pragma unroll
-    for (int k = 0; k < kCIpt; ++k) {
-        int32_t ee, oo;
-        sink_contrib(v[k], &ee, &oo);
-        e += ee;
-        o += oo;
-    }
-    int64_t xe, xo, te, to;
-    block_scan2(e, o, &xe, &xo, &te, &to);
-    if (threadIdx.x == 0) {
-        tiles[2 * blockIdx.x] = te;
-        tiles[2 * blockIdx.x + 1] = to;
-    }
-}
 
-// exclusive scan of the (even, odd) tile sums by one block; totals after the last tile
+// exclusive scan of the (even, odd) tile sums (tsum, summed by k_scatter) by
+// one block into tiles, totals after the last tile; tsum is cleared for the
+// next valuation. A single game whose sink slot is its last id needs no
+// k_game_prefix: its prefixes at its first id are zero and the odd prefix at
+// its sink slot is the odd total, which ranks the sink (sink_key >= 0 names it).
 constexpr int kTileScanThreads = 1024;
 
-__global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* tiles, int64_t ntiles) {
+__global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* __restrict__ tsum, int64_t* tiles,
+                                                                 int64_t ntiles, int32_t sink_key, int64_t* gscan,
+                                                                 int32_t* key, Counters* cnt) {
     __shared__ int64_t se[kTileScanThreads / 32], so[kTileScanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t ce = 0, co = 0;
     for (int64_t b = 0; b < ntiles; b += kTileScanThreads) {
         const int64_t i = b + threadIdx.x;
-        const int64_t e = i < ntiles ? tiles[2 * i] : 0, o = i < ntiles ? tiles[2 * i + 1] : 0;
+        const int64_t e = i < ntiles ? tsum[2 * i] : 0, o = i < ntiles ? tsum[2 * i + 1] : 0;
+        if (i < ntiles) {
+            tsum[2 * i] = 0;
+            tsum[2 * i + 1] = 0;
+        }
         int64_t xa = e, xb = o;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -752,6 +759,13 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* tiles,
     if (threadIdx.x == 0) {
         tiles[2 * ntiles] = ce;
         tiles[2 * ntiles + 1] = co;
+        if (sink_key >= 0) {
+            gscan[0] = 0;
+            gscan[1] = 0;
+            gscan[2] = co;
+            key[sink_key] = (int32_t)co;
+            cnt->sink_rank = (int32_t)co;
+        }
     }
 }
 
@@ -1161,6 +1175,7 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A((void**)&g->hugelist, sizeof(int32_t) * n));
     g->ntiles = std::max<int64_t>(1, (n + kCoopTile - 1) / kCoopTile);
     PG_CUDA_TRY(ctx, A((void**)&g->tiles, sizeof(int64_t) * (2 * g->ntiles + 2)));
+    PG_CUDA_TRY(ctx, A((void**)&g->tsum, sizeof(int64_t) * (2 * g->ntiles + 2)));
     PG_CUDA_TRY(ctx, A((void**)&g->gscan, sizeof(int64_t) * 3 * (size_t)g->ngames));
     PG_CUDA_TRY(ctx, A((void**)&g->gst, sizeof(GameState) * (size_t)g->ngames));
     PG_CUDA_TRY(ctx, A((void**)&g->gactive, sizeof(int32_t)));
@@ -1209,6 +1224,7 @@ pg_status reset_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->oddsz, 0, sizeof(int32_t) * n, s));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->ccnt, 0, sizeof(int32_t) * (n + 1), s));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->tsum, 0, sizeof(int64_t) * (2 * g->ntiles + 2), s));
     return reset_games(g);
 }
 
@@ -1249,7 +1265,8 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
     prof_end(g, KID_CSCAN, 3);
     prof_begin(g, KID_SCATTER);
-    k_scatter<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval);
+    k_scatter<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval,
+                                             g->tsum);
     prof_end(g, KID_SCATTER, 1);
     prof_begin(g, KID_SIBLINGS);
     k_siblings<<<grid, kBlock, 0, s>>>(n, g->coff, g->cl_ks, g->wgt, g->oddsz, g->plist, g->hugelist, c);
@@ -1261,13 +1278,17 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         void* args[] = {(void*)&n,        (void*)&g->gd32,   (void*)&g->sz,  (void*)&g->kind,  (void*)&g->hugelist,
                         (void*)&g->tiles, (void*)&ntiles,    (void*)&g->wgt, (void*)&g->oddsz, (void*)&c};
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_idscan_coop, g->coop_blocks, kBlock, args, 0, s));
-        k_sink_reduce<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles);
-        k_tiles_scan<<<1, kTileScanThreads, 0, s>>>(g->tiles, g->ntiles);
-        const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + 7) / 8, 4096));
-        k_game_prefix<<<gp, kBlock, 0, s>>>(n, g->ngames, g->gsink, g->sinkval, g->tiles, g->gscan, g->key, c);
+        // one game whose sink slot is its last id: the tile scan ranks the sink itself
+        const bool single = g->ngames == 1 && !g->vgame && g->sink0 == n - 1;
+        k_tiles_scan<<<1, kTileScanThreads, 0, s>>>(g->tsum, g->tiles, g->ntiles, single ? g->sink0 : -1, g->gscan,
+                                                    g->key, c);
+        if (!single) {
+            const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + 7) / 8, 4096));
+            k_game_prefix<<<gp, kBlock, 0, s>>>(n, g->ngames, g->gsink, g->sinkval, g->tiles, g->gscan, g->key, c);
+        }
         k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->vgame, g->gscan, g->wgt);
+        prof_end(g, KID_SINKSCAN, single ? 3 : 4);
     }
-    prof_end(g, KID_SINKSCAN, 5);
     prof_begin(g, KID_CHAIN2);
     k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key);
     prof_end(g, KID_CHAIN2, 1);

@@ -25,7 +25,7 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the arrays inside the static buffer, for kStaticMaxN vertices.
 struct Layout {
     size_t gd, gd32, plist, slot, ccnt, coff, cl_ks, sz, sinkval, wgt, oddsz, key, cls, kind, depth, hugelist,
-        flags, tiles, gst, gscan, gsink, cnt, scan, bytes;
+        flags, tiles, tsum, gst, gscan, gsink, cnt, scan, bytes;
 };
 
 constexpr Layout make_layout() {
@@ -51,6 +51,7 @@ constexpr Layout make_layout() {
     L.hugelist = p; p = al256(p + 4 * N);
     L.flags = p;    p = al256(p + N);
     L.tiles = p;    p = al256(p + 8 * (2 * ntiles + 2));
+    L.tsum = p;     p = al256(p + 8 * (2 * ntiles + 2));
     L.gst = p;      p = al256(p + sizeof(GameState));
     L.gscan = p;    p = al256(p + 3 * 8);
     L.gsink = p;    p = al256(p + 4);
@@ -164,6 +165,7 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     g.hugelist = (int32_t*)(base + kLayout.hugelist);
     g.flags = (uint8_t*)(base + kLayout.flags);
     g.tiles = (int64_t*)(base + kLayout.tiles);
+    g.tsum = (int64_t*)(base + kLayout.tsum);
     g.ntiles = std::max<int64_t>(1, ((int64_t)n + 1 + kCoopTile - 1) / kCoopTile);
     g.gst = (GameState*)(base + kLayout.gst);
     g.gscan = (int64_t*)(base + kLayout.gscan);
