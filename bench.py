@@ -163,19 +163,36 @@ def kernel_entry(name, v, s, hbm):
     return e
 
 
-# the source file of each kernel class whose DRAM traffic is recorded
-KERNEL_SOURCE = {"chain1": "pg_iter.cu", "walk": "pg_iter.cu", "chain2": "pg_iter.cu", "scatter": "pg_iter.cu",
-                 "siblings": "pg_iter.cu", "switch_odd": "pg_iter.cu"}
+# where each kernel class whose DRAM traffic is recorded is defined
+KERNEL_SOURCE = {"chain1": ("pg_iter.cu", "k_chain1(")}
+
+
+def kernel_text(path, marker):
+    """The source from the top of the file to the end of the definition that
+    ``marker`` opens (the kernel with the helpers and constants before it)."""
+    text = open(path, "rb").read()
+    i = text.index(marker.encode())
+    j = text.index(b"{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        c = text[k:k + 1]
+        if c == b"{":
+            depth += 1
+        elif c == b"}":
+            depth -= 1
+            if depth == 0:
+                return text[:k + 1]
+    return text
 
 
 def kernel_source_hash(kernel="chain1"):
-    """Hash of what the kernel is compiled from: its source file and the
-    compile-time constants of the internal header (host-side structures
-    elsewhere do not change the kernel)."""
+    """Hash of what the kernel is compiled from: its source up to the end of
+    its definition and the compile-time constants of the internal header
+    (code after it and host-side structures do not change it)."""
     csrc = os.path.join(ROOT, "paper_1705_02313_gb300", "csrc")
+    fname, marker = KERNEL_SOURCE.get(kernel, ("pg_iter.cu", "k_%s(" % kernel))
     h = hashlib.sha256()
-    with open(os.path.join(csrc, KERNEL_SOURCE.get(kernel, "pg_iter.cu")), "rb") as fh:
-        h.update(fh.read())
+    h.update(kernel_text(os.path.join(csrc, fname), marker))
     with open(os.path.join(csrc, "pg_internal.cuh"), "rb") as fh:
         for line in fh.read().splitlines():
             if line.strip().startswith(b"constexpr"):
