@@ -73,14 +73,26 @@ __global__ void k_mark_priorities(int32_t n, const int32_t* pri, int32_t shift_o
     }
 }
 
-__global__ void k_indegree(int64_t m, const int32_t* tgt, int32_t* indeg) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&indeg[tgt[e]], 1);
+// The reverse adjacency of the trap computation holds only the edges between
+// Odd vertices: U starts as the Odd vertices, and peeling only ever lowers the
+// counts of Odd predecessors of Odd vertices.
+__global__ void k_indegree(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* own, int32_t* indeg) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (own[v] != 1) continue;
+        for (int32_t e = off[v]; e < off[v + 1]; ++e)
+            if (own[tgt[e]] == 1) atomicAdd(&indeg[tgt[e]], 1);
+    }
 }
 
-__global__ void k_reverse_scatter(int32_t n, const int32_t* off, const int32_t* tgt, int32_t* fill, int32_t* radj) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        for (int32_t e = off[v]; e < off[v + 1]; ++e) radj[atomicAdd(&fill[tgt[e]], 1)] = (int32_t)v;
+__global__ void k_reverse_scatter(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* own,
+                                  int32_t* fill, int32_t* radj) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (own[v] != 1) continue;
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+            const int32_t t = tgt[e];
+            if (own[t] == 1) radj[atomicAdd(&fill[t], 1)] = (int32_t)v;
+        }
+    }
 }
 
 // U starts as every Odd vertex; cnt[v] = edges of v into Odd vertices. Odd
@@ -312,12 +324,12 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, T.get(&fill, (int64_t)n + 1));
     PG_CUDA_TRY(ctx, cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (size_t)n, s));
     ++ctx->launches;
-    k_indegree<<<nblocks(m), kBlock, 0, s>>>(m, tgt, indeg);
+    k_indegree<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, indeg);
     ctx->launches += 3;
     PG_CUDA_TRY(ctx, exclusive_scan_i32(indeg, roff, n, nullptr, stmp, stb, s));
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(fill, roff, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
     ++ctx->launches;
-    k_reverse_scatter<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, fill, radj);
+    k_reverse_scatter<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, fill, radj);
 
     // U: greatest fixpoint by peeling
     PG_CUDA_TRY(ctx, T.get(&cnt, n));
