@@ -308,3 +308,21 @@ def test_memory_pool_reuse_and_release(pg, ctx):
         assert np.array_equal(first[k], again[k]), k
     with pytest.raises(pg.PgError):
         pg.pg_release_cached_memory(-1)
+
+
+def test_memory_release_keeps_live_games(pg, ctx):
+    # releasing the cache while a game is loaded leaves that game intact
+    a = gen.random_game(50_000, 2, 5, 4)
+    b = gen.random_game(120_000, 2, 5, 5)
+    want = pg.solve_arrays(ctx, a.n, *a.arrays())
+    live = pg.pg_load_csr(ctx, a.n, a.m, *a.arrays())
+    try:
+        pg.solve_arrays(ctx, b.n, *b.arrays())  # loads, solves and frees another game
+        pg.pg_release_cached_memory(0)
+        win = np.empty(a.n, np.uint8)
+        sigma = np.empty(a.n, np.int32)
+        major, inner = pg.pg_solve(ctx, live, win=win, sigma=sigma)
+    finally:
+        pg.pg_game_free(live)
+    assert np.array_equal(win, want["win"]) and np.array_equal(sigma, want["sigma"])
+    assert (major, inner) == (want["major"], want["inner"])
