@@ -309,6 +309,12 @@ __device__ inline void hot_add(int32_t x, int32_t* tkey, int32_t* tcnt, int32_t*
     atomicAdd(sz + x, 1);
 }
 
+// k_chain1 walks three chains per thread: it is bound by issuing its walk
+// instructions, and a warp runs until the longest of its chains ends, so fewer
+// chains per warp waste fewer issue slots (two, three, four, six: 287, 280,
+// 290, 340 us per launch on the 10M game).
+constexpr int kIlpChain1 = 3;
+
 // Classification and g-subtree sizes. Each vertex walks its g-chain (4-byte
 // words) to its end: the sink means a finite valuation, a "none" vertex
 // means TOP (odd cycle if that cycle maximum is odd). Finite vertices then
@@ -331,13 +337,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t nfin = 0, nodd = 0;
-    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * kIlpChain1) < n;
          tile += nwarps) {
-        int32_t v[kIlp], g[kIlp], x[kIlp], cyc[kIlp], len[kIlp];
-        bool act[kIlp], sinkchild[kIlp], slotid[kIlp];
+        int32_t v[kIlpChain1], g[kIlpChain1], x[kIlpChain1], cyc[kIlpChain1], len[kIlpChain1];
+        bool act[kIlpChain1], sinkchild[kIlpChain1], slotid[kIlpChain1];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+        for (int j = 0; j < kIlpChain1; ++j) {
+            v[j] = (int32_t)((tile * 32 * kIlpChain1) + lane + 32 * j);
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
             const uint32_t w = (v[j] < n && !slotid[j]) ? gd32[v[j]] : kG32Sink;
             g[j] = g32_ptr(w);
@@ -350,11 +356,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
         // classification walks (len: the vertices from g(v) to the chain's end)
         for (;;) {
             bool any = false;
-            uint32_t wx[kIlp];
+            uint32_t wx[kIlpChain1];
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
+            for (int j = 0; j < kIlpChain1; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < kIlpChain1; ++j) {
                 if (act[j]) {
                     ++len[j];
                     if (g32_none(wx[j])) {
@@ -370,10 +376,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
             if (!any) break;
         }
         // finite vertices below a vertex parent: slot, then sizes along the chain
-        int32_t sl[kIlp];
-        bool deep[kIlp];
+        int32_t sl[kIlpChain1];
+        bool deep[kIlpChain1];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < kIlpChain1; ++j) {
             act[j] = v[j] < n && !slotid[j] && cyc[j] < 0 && !sinkchild[j];
             sl[j] = act[j] ? atomicAdd(ccnt + g[j], 1) : -1;
             x[j] = g[j];
@@ -381,9 +387,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
         }
         for (;;) {
             bool any = false;
-            uint32_t wx[kIlp];
+            uint32_t wx[kIlpChain1];
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < kIlpChain1; ++j) {
                 if (act[j]) {  // len[j]: the additions still to come on this chain, this one included
                     if (deep[j] && len[j] <= kHotTop) hot_add(x[j], tkey, tcnt, sz);
                     else atomicAdd(sz + x[j], 1);
@@ -392,7 +398,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
                 wx[j] = act[j] ? gd32[x[j]] : 0u;
             }
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < kIlpChain1; ++j) {
                 if (act[j]) {
                     x[j] = g32_ptr(wx[j]);
                     act[j] = !g32_sink(wx[j]);
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
             if (!any) break;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < kIlpChain1; ++j) {
             if (v[j] >= n) continue;
             if (slotid[j]) {
                 kind[v[j]] = kKSinkSlot;
