@@ -446,6 +446,8 @@ __device__ inline int32_t order_key(int32_t c, bool odd) { return odd ? -(c + 1)
 // (order key, subtree size); the sink's children record size and parity for
 // the id-ordered scan. Also clears the children counts for the next valuation.
 // kIlp vertices per thread, their parents' segment offsets gathered together.
+static_assert(kCoopTile % (32 * kIlp) == 0, "k_scatter sums each warp tile into one scan tile");
+
 __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* __restrict__ gd32,
                                                     const uint8_t* __restrict__ kind, const int32_t* __restrict__ sz,
                                                     const int32_t* __restrict__ coff, const int32_t* __restrict__ slot,
