@@ -142,7 +142,7 @@ def algorithmic_bytes(name, s):
         "child_scan": 8 * n,   # counts read, offsets written
         "scatter": 33 * n,     # kind 1, sz 4, gd32 4, slot 4, the parent's offset 4 read; entry 8, count 4, sink value 4 written
         "siblings": 20 * n,    # offsets 4, entries 8 read; weight 4, odd total 4 written
-        "sink_scan": 16 * n,   # sink values read twice, weights written
+        "sink_scan": 8 * n,    # sink values 4 read, weights 4 written (the tile sums come with k_scatter)
         "chain2": 17 * n,      # flags 1, odd total 4, weight 4, gd32 4 read; key 4 written
         "switch_odd": n + 12 * s["n_odd"] + 8 * s["m_odd"],
         "switch_even": n + 16 * s["n_even"] + 8 * s["m_even"],
