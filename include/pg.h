@@ -135,7 +135,8 @@ const char *pg_last_error(const pg_ctx *ctx);
 pg_status pg_load_csr(pg_ctx *ctx, int32_t n, int64_t m, const int32_t *offsets, const int32_t *targets,
                       const uint8_t *owner, const int32_t *pri, int32_t mem_kind, pg_game **out);
 
-/* Frees a game (NULL is ignored). */
+/* Frees a game (NULL is ignored). Waits for the work of every stream on the game's device (as cudaFree would),
+ * then returns the game's memory to the pool of pg_release_cached_memory. */
 void pg_game_free(pg_game *game);
 
 /* Sizes of a loaded game: original n and m, dummies k (any pointer may be NULL). */
