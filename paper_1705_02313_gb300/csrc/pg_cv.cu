@@ -31,8 +31,26 @@ __device__ inline i128 top_key() { return (i128)(~(unsigned __int128)0 >> 1); }
 
 __device__ inline int level_of(const Levels& L, int32_t v) {
     int l = 0;
-    while (l + 1 < L.n && v >= L.start[l + 1]) ++l;
+#pragma unroll
+    for (int i = 1; i < kMaxLevels; ++i) l += (i < L.n && v >= L.start[i]) ? 1 : 0;
     return l;
+}
+
+// The walks count the vertices they pass per level in 7-bit fields of one
+// word (a walk passes at most kWalkCap + 1 < 128 vertices in one kernel) and
+// turn the counts into the 128-bit weight once at the end.
+static_assert(kWalkCap + 1 < 128 && 7 * kMaxLevels <= 64, "per-level walk counts must fit 7-bit fields");
+__device__ inline uint64_t count_one(const Levels& L, int32_t v) { return 1ull << (7 * level_of(L, v)); }
+
+__device__ inline i128 weight_of_counts(const Levels& L, uint64_t c) {
+    i128 w = 0;
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l) {
+        if (l >= L.n) break;
+        const i128 d = (i128)((c >> (7 * l)) & 127u) << (kDigitBits * l);
+        w += ((L.odd_mask >> l) & 1u) ? -d : d;
+    }
+    return w;
 }
 
 __device__ inline i128 weight_of(const Levels& L, int32_t v) {
@@ -127,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
          tile += nwarps) {
         int32_t v[kIlpCv], x[kIlpCv];
         uint32_t d[kIlpCv];
-        i128 acc[kIlpCv];
+        uint64_t acc[kIlpCv];  // per-level counts of the vertices passed
         bool act[kIlpCv], slotid[kIlpCv];
 #pragma unroll
         for (int j = 0; j < kIlpCv; ++j) {
@@ -135,7 +153,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
             x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
             d[j] = 1;
-            acc[j] = (v[j] < n && !slotid[j]) ? weight_of(L, v[j]) : 0;
+            acc[j] = (v[j] < n && !slotid[j]) ? count_one(L, v[j]) : 0;
             act[j] = v[j] < n && !slotid[j] && x[j] < v[j];
         }
         for (;;) {
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
 #pragma unroll
             for (int j = 0; j < kIlpCv; ++j) {
                 if (act[j]) {
-                    acc[j] += weight_of(L, x[j]);
+                    acc[j] += count_one(L, x[j]);
                     x[j] = nx[j];
                     ++d[j];
                     act[j] = x[j] < v[j];
@@ -166,8 +184,9 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
                 gd[v[j]] = w;
                 gdB[v[j]] = w;
                 gd32[v[j]] = g32_word(w);
-                ws[v[j]] = acc[j];
-                wsB[v[j]] = acc[j];
+                const i128 wt = weight_of_counts(L, acc[j]);
+                ws[v[j]] = wt;
+                wsB[v[j]] = wt;
             }
             const unsigned m = __ballot_sync(kFullMask, pend);
             if (m) {
@@ -196,6 +215,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_more_cv(Levels L, const int32_t
         int32_t v[kIlpCv], x[kIlpCv];
         uint32_t d[kIlpCv];
         i128 acc[kIlpCv];
+        uint64_t lc[kIlpCv];  // per-level counts of the vertices passed in this kernel
         bool act[kIlpCv], in[kIlpCv];
 #pragma unroll
         for (int j = 0; j < kIlpCv; ++j) {
@@ -206,6 +226,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_more_cv(Levels L, const int32_t
             x[j] = gd_ptr(w);
             d[j] = gd_dist(w);
             acc[j] = in[j] ? ws[v[j]] : 0;
+            lc[j] = 0;
             act[j] = in[j] && x[j] < v[j];
         }
         for (;;) {
@@ -219,7 +240,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_more_cv(Levels L, const int32_t
 #pragma unroll
             for (int j = 0; j < kIlpCv; ++j) {
                 if (act[j]) {
-                    acc[j] += weight_of(L, x[j]);
+                    lc[j] += count_one(L, x[j]);
                     x[j] = nx[j];
                     ++d[j];
                     act[j] = x[j] < v[j];
@@ -236,8 +257,9 @@ __global__ void __launch_bounds__(kBlock) k_walk_more_cv(Levels L, const int32_t
                 gd[v[j]] = w;
                 gdB[v[j]] = w;
                 gd32[v[j]] = g32_word(w);
-                ws[v[j]] = acc[j];
-                wsB[v[j]] = acc[j];
+                const i128 wt = acc[j] + weight_of_counts(L, lc[j]);
+                ws[v[j]] = wt;
+                wsB[v[j]] = wt;
             }
             const unsigned m = __ballot_sync(kFullMask, pend);
             if (m) {
