@@ -11,10 +11,20 @@ step, preprocessing and Even switches included).
 
 N > 1 (launched by torch.distributed.run): every rank solves its own replica
 of the game (a single game does not shard: replicas only); value = edges *
-valuations summed over ranks / the slowest rank's time.
+valuations summed over ranks / the slowest rank's time. The batch leg shards
+its games over the ranks instead (each rank solves its share alone).
 --impl reference times the CPU oracle (oracle/o2.c, single thread) on a
 bounded sample of the same workload: each step runs the first iterations of
 the same solve.
+
+Beside the headline the line carries: the end-to-end rate from pinned host
+memory, the dominant kernel against the measured HBM bandwidth (with its DRAM
+traffic from the committed ncu summary while the kernel's source is
+unchanged), per-kernel times, SI-Reset, the 4-priority count-vector game, the
+256-game batch (--batch batch-4096 for the large one), a Poisson serving
+stream (--serve seconds), an optional long-chain valuation (--chain n), and
+the oracle timed on the host cores (one core for the solve; all cores, one
+game per process, for the batch and serving samples).
 """
 from __future__ import annotations
 
