@@ -78,3 +78,16 @@ def test_native_batch_matches_packed_numpy_batch():
     got = gen.native_batch(37, 3, 30000, 2, 6, nthreads=4)
     for x, y in zip(want, got):
         assert np.array_equal(x, y)
+
+
+def test_native_batch_subset_packs_the_same_games():
+    # one rank's share of a batch (indices, in any order) holds exactly those games of the whole batch
+    vb, eb, off, tgt, own, pri = gen.native_batch(12, 50, 900, 1, 5)
+    idx = [9, 2, 11, 0]
+    vb2, eb2, off2, tgt2, own2, pri2 = gen.native_batch(12, 50, 900, 1, 5, indices=idx)
+    assert int(vb2[-1]) == sum(int(vb[i + 1] - vb[i]) for i in idx)
+    for k, i in enumerate(idx):
+        a, b, c, d = int(vb[i]), int(vb[i + 1]), int(vb2[k]), int(vb2[k + 1])
+        assert np.array_equal(pri[a:b], pri2[c:d]) and np.array_equal(own[a:b], own2[c:d])
+        assert np.array_equal(tgt[eb[i]:eb[i + 1]], tgt2[eb2[k]:eb2[k + 1]])
+        assert np.array_equal(off[a + i:b + i + 1], off2[c + k:d + k + 1])
