@@ -18,11 +18,12 @@ bounded sample of the same workload: each step runs the first iterations of
 the same solve.
 
 Beside the headline the line carries: the end-to-end rate from pinned host
-memory, the dominant kernel against the measured HBM bandwidth (with its DRAM
-traffic from the committed ncu summary while the kernel's source is
-unchanged), per-kernel times, SI-Reset, the 4-priority count-vector game, the
-256-game batch (--batch batch-4096 for the large one), a Poisson serving
-stream (--serve seconds), an optional long-chain valuation (--chain n), and
+memory, the roofline of the inner iteration (B_alg = 8 m' + 20 n' bytes per
+valuation + switching pass, over the solve time of the timed steps, against
+the measured HBM bandwidth; DRAM traffic from the committed ncu summary while
+the kernels' sources are unchanged), the dominant kernel, per-kernel times, SI-Reset, the 4-priority count-vector game, the
+4,096-game batch (--batch batch-256 for a small one), a Poisson serving
+stream (--serve seconds, 60 by default), an optional long-chain valuation (--chain n), and
 the oracle timed on the host cores (one core for the solve; all cores, one
 game per process, for the batch and serving samples).
 """
@@ -175,6 +176,8 @@ def kernel_entry(name, v, s, hbm):
 
 # where each kernel class whose DRAM traffic is recorded is defined
 KERNEL_SOURCE = {"chain1": ("pg_iter.cu", "k_chain1(")}
+# the files holding the kernels of one inner iteration (their traffic is recorded as "iteration")
+ITERATION_SOURCES = ("pg_iter.cu", "pg_scan.cu")
 
 
 def kernel_text(path, marker):
@@ -200,9 +203,14 @@ def kernel_source_hash(kernel="chain1"):
     its definition and the compile-time constants of the internal header
     (code after it and host-side structures do not change it)."""
     csrc = os.path.join(ROOT, "paper_1705_02313_gb300", "csrc")
-    fname, marker = KERNEL_SOURCE.get(kernel, ("pg_iter.cu", "k_%s(" % kernel))
     h = hashlib.sha256()
-    h.update(kernel_text(os.path.join(csrc, fname), marker))
+    if kernel == "iteration":  # every kernel of one inner iteration: the whole files they are compiled from
+        for fname in ITERATION_SOURCES:
+            with open(os.path.join(csrc, fname), "rb") as fh:
+                h.update(fh.read())
+    else:
+        fname, marker = KERNEL_SOURCE.get(kernel, ("pg_iter.cu", "k_%s(" % kernel))
+        h.update(kernel_text(os.path.join(csrc, fname), marker))
     with open(os.path.join(csrc, "pg_internal.cuh"), "rb") as fh:
         for line in fh.read().splitlines():
             if line.strip().startswith(b"constexpr"):
@@ -530,9 +538,12 @@ def serve_measure(name, seconds, cpu_budget=0):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample
 
-def cpu_sample(game, iters):
+def cpu_sample(game, iters, gp=None):
+    """The oracle's first ``iters`` valuations of the solve (the preprocessing
+    is outside the timed part; pass ``gp`` to reuse it)."""
     from oracle import o2
-    gp = o2.preprocess(game.n, game.offsets, game.targets, game.owner, game.pri)
+    if gp is None:
+        gp = o2.preprocess(game.n, game.offsets, game.targets, game.owner, game.pri)
     t0 = time.perf_counter()
     res = o2.run(gp, max_inner=iters, allow_timeout=True)
     dt = time.perf_counter() - t0
@@ -586,11 +597,13 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import o2
     game = make_game(args.workload)
+    gp = o2.preprocess(game.n, game.offsets, game.targets, game.owner, game.pri)
     iters = args.ref_iters
     times = []
     for i in range(args.warmup + args.steps):
-        r = cpu_sample(game, iters)
+        r = cpu_sample(game, iters, gp)
         if i >= args.warmup:
             times.append(r["seconds"])
     tot = sum(times)
@@ -639,8 +652,14 @@ def run_ours(args):
                val_depth=torch.empty(n, dtype=torch.int32, device=dev),
                val_rank=torch.empty(n, dtype=torch.int32, device=dev))
 
-    def step(inputs, outputs):
+    def step(inputs, outputs, evs=None):
+        """One load + solve; evs: three CUDA events recorded on the library's
+        stream before the load, between load and solve, and after the solve."""
+        if evs:
+            evs[0].record(stream)
         g = pg.pg_load_csr(ctx, n, m, *inputs)
+        if evs:
+            evs[1].record(stream)
         try:
             _, _, k = pg.pg_game_info(g)
             like = outputs["win"]
@@ -649,6 +668,8 @@ def run_ours(args):
             else:
                 ds = torch.empty(max(k, 1), dtype=torch.int8).pin_memory()
             major, inner = pg.pg_solve(ctx, g, dummy_sigma=ds, **outputs)
+            if evs:
+                evs[2].record(stream)
             stats = pg.pg_kernel_stats(g)
             return major, inner, k, stats, pg.pg_last_timing(g)
         finally:
@@ -672,14 +693,19 @@ def run_ours(args):
     ev0.record(stream)
     t0 = time.perf_counter()
     inner_total = 0
+    step_evs = []
     for _ in range(args.steps):
-        _, inner_s, _, _, _ = step(d_in, out)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        _, inner_s, _, _, _ = step(d_in, out, evs)
+        step_evs.append(evs)
         inner_total += inner_s
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t0
     dev_ms = ev0.elapsed_time(ev1)
+    load_ms = sum(e[0].elapsed_time(e[1]) for e in step_evs)
+    solve_ms = sum(e[1].elapsed_time(e[2]) for e in step_evs)
     launches = pg.pg_launch_count(ctx) - launches0
     clk = clocks.stop()
     t_ms = max(dev_ms, 0.0)
@@ -711,7 +737,8 @@ def run_ours(args):
     d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + k
     e2e = {"value": m * e_inner / e_wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel class
+    # roofline: the inner iteration against B_alg = 8 m' + 20 n' (one pass over the edges and a few per-id arrays),
+    # its time taken from the timed steps (solve time, CUDA events around pg_solve, over the valuations computed)
     own = game.owner
     deg = np.diff(game.offsets).astype(np.int64)
     s = {"n": n + k, "m": m + k, "n_odd": int(own.sum()), "m_odd": int(deg[own == 1].sum()),
@@ -719,23 +746,34 @@ def run_ours(args):
     per = {nm: (ms, launches_k, calls) for nm, (ms, launches_k, calls) in kstats.items() if calls > 0}
     dom_name = max(per, key=lambda x: per[x][0]) if per else None
     hbm, src = peaks()
-    roof = None
+    b_alg = 8 * (m + k) + 20 * (n + k)
+    iter_s = solve_ms / 1000.0 / max(inner_total, 1)
+    roof = {"bound": "hbm", "kernel": "inner iteration (valuation + switching, the CUDA-graph loop of pg_solve)",
+            "achieved": b_alg / iter_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": b_alg / iter_s / 1e9 / hbm,
+            "peak_source": src + " (hbm_gbs, burst copy)", "traffic": measured_traffic("iteration", args.workload),
+            "algorithmic_bytes_per_launch": b_alg, "avg_launch_us": iter_s * 1e6,
+            "units": "one inner iteration: B_alg = 8 m' + 20 n' bytes, m' = %d edges and n' = %d vertices of G'"
+                     % (m + k, n + k),
+            "timing": "solve time of the timed steps (CUDA events around pg_solve on the library's stream) / "
+                      "valuations; the loads (%.2f ms per step) are outside" % (load_ms / args.steps),
+            "inner_loop_edges_per_s": m / iter_s}
+    dominant = None
     if dom_name:
         ms, _, calls = per[dom_name]
         avg_s = ms / calls / 1000.0
         ab = algorithmic_bytes(dom_name, s)
         ach = ab / avg_s / 1e9 if ab else None
-        roof = {"bound": "hbm", "kernel": dom_name, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": (ach / hbm if ach else None), "peak_source": src + " (hbm_gbs, burst copy)",
-                "traffic": measured_traffic(dom_name, args.workload),
-                "algorithmic_bytes_per_launch": ab, "avg_launch_us": avg_s * 1e6}
+        dominant = {"kernel": dom_name, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": (ach / hbm if ach else None), "traffic": measured_traffic(dom_name, args.workload),
+                    "algorithmic_bytes_per_launch": ab, "avg_launch_us": avg_s * 1e6,
+                    "timing": "host-driven timing pass (per-kernel CUDA events)"}
     valuation_path = None
     if tinfo["valuations"]:
         per_iter_s = (tinfo["valuation_ms"] + tinfo["switch_ms"]) / tinfo["valuations"] / 1000.0
-        b_alg = 8 * (m + k) + 20 * (n + k)
         valuation_path = {"inner_iteration_us": per_iter_s * 1e6, "b_alg_bytes": b_alg,
                           "achieved_gbs": b_alg / per_iter_s / 1e9, "frac_of_hbm": b_alg / per_iter_s / 1e9 / hbm,
-                          "inner_loop_edges_per_s": m / per_iter_s}
+                          "inner_loop_edges_per_s": m / per_iter_s,
+                          "timing": "host-driven timing pass (one launch per kernel, events around each class)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -748,7 +786,9 @@ def run_ours(args):
         "full_solve_ms": t_ms / args.steps,
         "wall_s": wall,
         "roofline": roof,
-        "inner_iteration": valuation_path,
+        "dominant_kernel": dominant,
+        "inner_iteration_host_loop": valuation_path,
+        "load_ms": load_ms / args.steps,
         "kernels": {nm: kernel_entry(nm, v, s, hbm) for nm, v in kstats.items() if v[1]},
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -841,9 +881,9 @@ def main():
                     help="also time pg_valuate on one successor chain of this many vertices (0: skip)")
     ap.add_argument("--cv-workload", default="random-10m-4pri",
                     help="count-vector workload measured beside the main line ('' to skip)")
-    ap.add_argument("--serve", type=float, default=10.0,
+    ap.add_argument("--serve", type=float, default=60.0,
                     help="seconds of the Poisson serving stream measured beside the main line (0: skip)")
-    ap.add_argument("--batch", choices=sorted(BATCHES), default="batch-256",
+    ap.add_argument("--batch", choices=sorted(BATCHES), default="batch-4096",
                     help="batch workload measured beside the main line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -130,8 +130,10 @@ const char *pg_last_error(const pg_ctx *ctx);
  * in Odd's Even-free trap) and the internal relabelling. Returns PG_EINVAL
  * for a malformed CSR (bad offsets, a vertex without edges, a target out of
  * range, an owner other than 0/1, a negative priority, sizes beyond 2^30
- * vertices or 2^31-1 edges after preprocessing) and PG_EUNSUPPORTED for
- * repeated priorities. */
+ * vertices or 2^31-1 edges after preprocessing). Repeated priorities load in
+ * count-vector mode (Section 5 with the count vectors of Section 3); such a
+ * game returns PG_EUNSUPPORTED only beyond that mode's limits, more than 5
+ * distinct priorities after preprocessing or 2^24 or more vertices. */
 pg_status pg_load_csr(pg_ctx *ctx, int32_t n, int64_t m, const int32_t *offsets, const int32_t *targets,
                       const uint8_t *owner, const int32_t *pri, int32_t mem_kind, pg_game **out);
 
@@ -142,7 +144,6 @@ void pg_game_free(pg_game *game);
 /* Sizes of a loaded game: original n and m, dummies k (any pointer may be NULL). */
 pg_status pg_game_info(const pg_game *game, int32_t *n, int64_t *m, int32_t *k);
 
-/* The vertex each dummy guards: out[j] = w for dummy j (k entries, host memory). */
 /* Counters of the last valuation on game (instrumentation): walks that ran
  * out of direct steps and were finished by pointer jumping, the jumping
  * rounds, finite vertices, vertices reaching an odd cycle, parents ranked
@@ -158,6 +159,8 @@ pg_status pg_game_counters(const pg_game *game, pg_counters *out);
  * entries) their values in G' (original priority + 2; 0 for the dummies), in
  * ascending order: column l of val_counts counts level_pri[l]. */
 pg_status pg_game_levels(const pg_game *game, int32_t *d, int32_t *level_pri);
+
+/* The vertex each dummy guards: out[j] = w for dummy j (k entries, host memory). */
 pg_status pg_game_dummies(const pg_game *game, int32_t *out);
 
 /* Full solve: Algorithm 1 (Section 4) from sigma_init (every Even vertex to
@@ -326,11 +329,12 @@ pg_status pg_best_response_bf(pg_game *game, const int32_t *sigma, const int8_t 
 
 /* Valuation of one successor function without allocating any memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
- * allocate device memory themselves or let a library do it, for example code
- * running while a CUDA graph is being captured, or a host framework that owns
- * every device allocation. Instead of per-game buffers it uses one fixed array
- * compiled into the library (about 18 MB of device memory, held by every GPU
- * that loads the library until the process exits).
+ * have this library allocate device memory for them, for example a host
+ * framework that reserves the device's memory up front and owns every
+ * allocation, or a latency-bound loop that must not call cudaMalloc (which can
+ * synchronise the device) while it runs. Instead of per-game buffers it uses
+ * one fixed array compiled into the library (about 19 MB of device memory,
+ * held by every GPU that loads the library until the process exits).
  *
  * Input, all device pointers owned by the caller:
  *   n     vertex count, 1 <= n <= 262,144 (2^18); larger n returns PG_EUNSUPPORTED
@@ -342,18 +346,21 @@ pg_status pg_best_response_bf(pg_game *game, const int32_t *sigma, const int8_t 
  * Output, device pointers owned by the caller (each may be NULL): val_class,
  * val_depth and val_rank with the meaning given at the top of this file; ranks
  * are positions among the finite valuations of these n vertices and the sink.
- * stream: a cudaStream_t (NULL = the legacy default stream); the call returns
- * after its work on the stream is complete.
+ * stream: a cudaStream_t (NULL = the legacy default stream). The call enqueues
+ * its work on the stream and then waits for the stream once, to read its error
+ * words; it returns after its work is complete.
  *
  * Returns PG_OK, PG_ENOTADMISSIBLE if a play reaches a cycle whose largest
  * priority is odd (outputs are still filled), PG_EINVAL for a NULL input or a
- * successor outside [0, n], PG_ECUDA for a CUDA error. No message is recorded.
+ * successor outside [0, n] (outputs are then unspecified), PG_ECUDA for a CUDA
+ * error. No message is recorded.
  *
  * Set-up: the first call on a device (with that device current) looks up the
- * fixed array's device address and the cooperative launch size; make that
- * first call before any stream capture. All calls share the array and it keeps
- * the last call's contents (each call clears what must start at zero), so calls
- * that overlap on the GPU, from any thread or stream, race: serialise them. */
+ * fixed array's device address and the cooperative launch size and keeps them
+ * for the life of the process (so a cudaDeviceReset on that device must not be
+ * followed by further calls). All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero), so calls that
+ * overlap on the GPU, from any thread or stream, race: serialise them. */
 pg_status pg_valuate_static(int32_t n, const int32_t *succ, const uint8_t *odd, int8_t *val_class,
                             int32_t *val_depth, int32_t *val_rank, void *stream);
 

@@ -6,10 +6,13 @@
 // sized for kStaticMaxN vertices. Host code cannot use the array's name as a
 // device address, so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it. The call
-// then lays out the valuation's arrays inside the static buffer, runs the
-// same kernels as pg_valuate on them, and copies class, depth and rank into
-// the caller's arrays. No device or host memory is allocated on any path;
-// error messages are not recorded (only the status is returned).
+// then lays out the valuation's arrays inside the static buffer, copies the
+// successor function into it (a successor outside [0, n] is recorded and
+// replaced by the sink, so no kernel reads out of bounds), runs the same
+// kernels as pg_valuate on the copy, writes class, depth and rank into the
+// caller's arrays and waits for its stream once, at the end, to read the
+// error words. No device or host memory is allocated on any path; error
+// messages are not recorded (only the status is returned).
 #include <mutex>
 
 #include "pg_internal.cuh"
@@ -24,7 +27,7 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the arrays inside the static buffer, for kStaticMaxN vertices.
 struct Layout {
-    size_t gd, gd32, plist, slot, ccnt, coff, cl_ks, sz, sinkval, wgt, oddsz, key, cls, kind, depth, hugelist,
+    size_t succ, bad, gd, gd32, plist, slot, ccnt, coff, cl_ks, sz, sinkval, wgt, oddsz, key, cls, kind, depth, hugelist,
         flags, tiles, tsum, gst, gscan, gsink, cnt, scan, bytes;
 };
 
@@ -33,6 +36,8 @@ constexpr Layout make_layout() {
     const size_t ntiles = (N + kCoopTile - 1) / kCoopTile;
     Layout L{};
     size_t p = 0;
+    L.succ = p;     p = al256(p + 4 * N);
+    L.bad = p;      p = al256(p + 4);
     L.gd = p;       p = al256(p + 8 * N);
     L.gd32 = p;     p = al256(p + 4 * N);
     L.plist = p;    p = al256(p + 4 * N);
@@ -71,19 +76,29 @@ unsigned char* g_static_addr[kMaxDevices] = {};
 int g_static_coop[kMaxDevices] = {};
 int g_static_chain1[kMaxDevices] = {};
 std::mutex g_static_mu;
-Counters g_static_hcnt;  // host copy of the counters (pageable, fixed)
+Counters g_static_hcnt;  // host copies of the counters and of the range-check word (pageable, fixed)
+int32_t g_static_hbad;
 
-// flags and range check: succ must be in [0, n]; id n is the sink slot
+// Copies the successor function into the buffer, sets the flags and checks
+// the range: a successor outside [0, n] is counted in *bad and replaced by
+// the sink (id n is the sink slot), so that no later kernel reads outside the
+// buffer. *bad must be zero before the launch.
 __global__ void k_static_prepare(int32_t n, const int32_t* __restrict__ succ, const uint8_t* __restrict__ odd,
-                                 uint8_t* __restrict__ flags, int32_t* gsink, Counters* cnt) {
+                                 int32_t* __restrict__ succ_copy, uint8_t* __restrict__ flags, int32_t* gsink,
+                                 int32_t* bad) {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
         if (v == n) {
             flags[v] = kSinkSlot;
+            succ_copy[v] = n;
             *gsink = n;
             continue;
         }
-        const int32_t s = succ[v];
-        if (s < 0 || s > n) atomicOr(&cnt->err, 1);
+        int32_t s = succ[v];
+        if (s < 0 || s > n) {
+            atomicAdd(bad, 1);
+            s = n;
+        }
+        succ_copy[v] = s;
         flags[v] = odd[v] ? kPriOdd : 0;
     }
 }
@@ -146,7 +161,7 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     g.n = n + 1;  // the vertices and the sink slot
     g.sink0 = n;
     g.ngames = 1;
-    g.strat = const_cast<int32_t*>(succ);  // read only by the valuation, never at the sink slot
+    g.strat = (int32_t*)(base + kLayout.succ);  // the checked copy of succ
     g.gd = (uint64_t*)(base + kLayout.gd);
     g.gd32 = (uint32_t*)(base + kLayout.gd32);
     g.plist = (int32_t*)(base + kLayout.plist);
@@ -178,13 +193,11 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     g.chain1_blocks = chain1;
 
     cudaStream_t s = ctx.stream;
-    if (cudaMemsetAsync(g.cnt, 0, sizeof(Counters), s) != cudaSuccess) return PG_ECUDA;
+    int32_t* bad = (int32_t*)(base + kLayout.bad);
+    if (cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess) return PG_ECUDA;
     k_static_prepare<<<(unsigned)std::min<int64_t>(((int64_t)n + kBlock) / kBlock, 4096), kBlock, 0, s>>>(
-        n, succ, odd, g.flags, g.gsink, g.cnt);
-    if (cudaMemcpyAsync(&g_static_hcnt, g.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return PG_ECUDA;
-    if (g_static_hcnt.err) return PG_EINVAL;
+        n, succ, odd, g.strat, g.flags, g.gsink, bad);
+    if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
 
     st = reset_scratch(&g);  // the buffer keeps the previous call's contents
     if (st == PG_OK) st = enqueue_valuation(&g, false);
@@ -193,7 +206,11 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     k_static_results<<<(unsigned)std::min<int64_t>(((int64_t)n + kBlock - 1) / kBlock, 4096), kBlock, 0, s>>>(
         n, g.cls, g.depth, g.key, val_class, val_depth, val_rank);
     if (cudaGetLastError() != cudaSuccess) return PG_ECUDA;
+    // the one wait of the call: the range-check word, then the counters (sync_counters waits for the stream)
+    if (cudaMemcpyAsync(&g_static_hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PG_ECUDA;
     st = sync_counters(&g);
     if (st != PG_OK) return st;
+    if (g_static_hbad) return PG_EINVAL;
     return g_static_hcnt.n_odd > 0 ? PG_ENOTADMISSIBLE : PG_OK;
 }
