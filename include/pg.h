@@ -381,6 +381,20 @@ pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuatio
  * synchronises once per iteration. Both give identical results. The paper has
  * no counterpart (it concerns launching work on the device only). */
 pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
+/* What each iteration of the loops of pg_solve / pg_best_response /
+ * pg_solve_batch / the server computes for switching (distinct priorities;
+ * count-vector games always rank). By default (enable = 0) an iteration builds
+ * the nearest-greater forest of the profile (Section 5's pseudoforest) and the
+ * class of every vertex, and the switching passes compare the valuations of
+ * two successors by walking their chains in that forest to their lowest
+ * common ancestor: the larger of the two vertices passed last decides by the
+ * parity of its priority (the order of Section 3). The exact ranks, depths and
+ * classes of the outputs come from one full valuation after the loop. With
+ * enable = 1 every iteration ranks all valuations (the full valuation of
+ * pg_valuate) and switches by rank. Both give identical results; the first
+ * does less work per iteration. */
+pg_status pg_set_loop_ranks(pg_ctx *ctx, int32_t enable);
+
 /* graph: 1 if the last loop on game ran as a graph, else 0; iterations: the
  * valuations it computed (each may be NULL). */
 pg_status pg_last_loop(const pg_game *game, int32_t *graph, int64_t *iterations);

@@ -327,9 +327,10 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t* gactive
 
 // One iteration of Algorithm 1 for every game of g (enqueued on ctx->stream).
 pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
-    pg_status st = enqueue_valuation(g, false);
-    if (!st) st = enqueue_switch(g, 1);
-    if (!st && even) st = enqueue_switch(g, 0);
+    const bool cmp = loop_compares(g);
+    pg_status st = cmp ? enqueue_valuation_cmp(g) : enqueue_valuation(g, false);
+    if (!st) st = cmp ? enqueue_switch_cmp(g, 1) : enqueue_switch(g, 1);
+    if (!st && even) st = cmp ? enqueue_switch_cmp(g, 0) : enqueue_switch(g, 0);
     if (!st) st = enqueue_bookkeeping(g, cap, even);
     if (!st && even && g->reset_tau) st = enqueue_reset(g);
     return st;
@@ -341,7 +342,8 @@ pg_status enqueue_iteration(pg_game* g, int64_t cap, bool even) {
 bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     const int w = even ? 1 : 0;
-    if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit && g->loop_reset[w] == g->reset_tau)
+    if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit && g->loop_reset[w] == g->reset_tau &&
+        g->loop_cmp[w] == loop_compares(g))
         return true;
     if (g->loop_exec[w]) {
         cudaGraphExecDestroy(g->loop_exec[w]);
@@ -407,6 +409,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     g->loop_cap[w] = cap;
     g->loop_limit[w] = limit;
     g->loop_reset[w] = g->reset_tau;
+    g->loop_cmp[w] = loop_compares(g);
     return true;
 }
 
@@ -424,6 +427,8 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
 pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     g->last_graph = false;
+    const bool cmp = loop_compares(g);
+    g->last_cmp = cmp;
     const int64_t hard = limit > 0 ? std::min<int64_t>(limit, cap + 2) : cap + 2;
     if (!tm.on && ctx->graphs && build_loop_graph(g, cap, even, hard)) {
         const int w = even ? 1 : 0;
@@ -444,11 +449,11 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
     }
     for (int64_t it = 1;; ++it) {
         tm.mark(0);
-        pg_status st = enqueue_valuation(g, false);
+        pg_status st = cmp ? enqueue_valuation_cmp(g) : enqueue_valuation(g, false);
         if (st) return st;
         tm.mark(1);
-        st = enqueue_switch(g, 1);
-        if (!st && even) st = enqueue_switch(g, 0);
+        st = cmp ? enqueue_switch_cmp(g, 1) : enqueue_switch(g, 1);
+        if (!st && even) st = cmp ? enqueue_switch_cmp(g, 0) : enqueue_switch(g, 0);
         if (!st) st = enqueue_bookkeeping(g, cap, even);
         if (!st && even && g->reset_tau) st = enqueue_reset(g);
         if (st) return st;
@@ -513,6 +518,12 @@ pg_status pg_release_cached_memory(int device) {
 pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;
     ctx->graphs = enable != 0;
+    return PG_OK;
+}
+
+pg_status pg_set_loop_ranks(pg_ctx* ctx, int32_t enable) {
+    if (!ctx) return PG_EINVAL;
+    ctx->loop_ranks = enable != 0;
     return PG_OK;
 }
 
@@ -630,10 +641,11 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
     if (gs.phase == kPhaseOddCycle)
         return fail(ctx, PG_ENOTADMISSIBLE, "pg_solve: an odd cycle was reached: sigma is not admissible");
     const bool timed_out = gs.phase == kPhaseTimeout;
-    if (timed_out) {
-        st = enqueue_valuation(g, false);  // valuation of the profile being returned
+    if (timed_out || g->last_cmp) {
+        st = enqueue_valuation(g, false);  // the full valuation of the profile being returned
         if (!st) st = sync_counters(g);
         if (st) return st;
+        g->last_cmp = false;
     }
     tm.mark(2);
     g->t_total = tm.since(3, 2);
@@ -666,6 +678,8 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
     if (gs.phase == kPhaseOddCycle)
         return fail(ctx, PG_ENOTADMISSIBLE, "an odd cycle was reached: sigma is not admissible");
     const bool timed_out = gs.phase == kPhaseTimeout;
+    st = finish_loop(g);  // ranks of the best response's valuation
+    if (st) return st;
     tm.mark(2);
     g->t_total = tm.since(3, 2);
     st = write_outputs(g, mem_kind, nullptr, nullptr, tau_inout, nullptr, nullptr, nullptr, nullptr, nullptr);

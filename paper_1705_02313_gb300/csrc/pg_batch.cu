@@ -261,10 +261,11 @@ pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int6
         any_timeout |= x.phase == kPhaseTimeout;
         any_odd |= x.phase == kPhaseOddCycle;
     }
-    if (any_timeout) {
+    if (any_timeout || g->last_cmp) {  // the full valuation of the profiles being returned
         st = enqueue_valuation(g, false);
         if (!st) st = sync_counters(g);
         if (st) return st;
+        g->last_cmp = false;
     }
     tm.mark(2);
     g->t_total = tm.since(3, 2);

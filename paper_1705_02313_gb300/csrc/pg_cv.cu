@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kBlock) k_chain_cv(int32_t n, const uint32_t* 
                                                      uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
                                                      int32_t* __restrict__ dom, int want_dom, GameState* gst,
                                                      Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t nfin = 0, nodd = 0;

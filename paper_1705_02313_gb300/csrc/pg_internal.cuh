@@ -97,6 +97,7 @@ enum KernelId {
     KID_CHAIN2,      // k_chain2
     KID_SWITCH_ODD,  // k_switch for Odd
     KID_SWITCH_EVEN, // k_switch for Even
+    KID_CLASSIFY,    // k_classify (loop iterations that compare valuations instead of ranking them)
     KID_COUNT
 };
 extern const char* const kKernelNames[KID_COUNT];
@@ -125,6 +126,7 @@ struct pg_ctx {
     int64_t launches = 0;       // kernels launched through this context
     bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
     bool graphs = true;         // run the iteration loop as one CUDA graph with a device-side condition
+    bool loop_ranks = false;    // loop iterations rank every valuation (else they only compare them)
     cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
 
@@ -227,8 +229,10 @@ struct pg_game {
     int64_t loop_launch[2] = {0, 0};                  // kernels per iteration of each graph
     int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
     bool last_graph = false;     // the last loop ran as a graph
+    bool last_cmp = false;       // the last loop compared valuations: key, cls and depth are not the current ones
     bool reset_tau = false;      // SI-Reset (Section 6): Odd restarts from its first edges after every Even switch
     bool loop_reset[2] = {false, false};  // the SI-Reset setting each loop graph was built with
+    bool loop_cmp[2] = {false, false};    // each loop graph compares valuations (loop_compares)
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;
@@ -313,6 +317,13 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom);
 pg_status enqueue_depth(pg_game* g);
 // Enqueues one switching pass for player (0 Even, 1 Odd) using g->key. No host synchronisation.
 pg_status enqueue_switch(pg_game* g, int player);
+// The loop's iterations without ranks: the nearest-greater forest and the class of every vertex, then
+// switching passes that compare the valuations of two successors by walking their g-chains.
+bool loop_compares(const pg_game* g);
+pg_status enqueue_valuation_cmp(pg_game* g);
+pg_status enqueue_switch_cmp(pg_game* g, int player);
+// After a loop that compared valuations: the full valuation of the current profile (key, cls, depth).
+pg_status finish_loop(pg_game* g);
 // Copies the counters to g->hcnt and waits for the stream; checks device error bits.
 pg_status sync_counters(pg_game* g);
 // Count-vector mode (pg_cv.cu): scratch, one valuation, one switching pass, counts output.

@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
                                                    uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
                                                    int32_t* __restrict__ dom, int want_dom,
                                                    const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
     __shared__ int32_t tkey[kHotSlots], tcnt[kHotSlots];
     for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
         tkey[i] = -1;
@@ -942,7 +943,9 @@ __global__ void __launch_bounds__(kBlock) k_idscan_coop(int32_t n, const uint32_
 // rank above everything).
 __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __restrict__ gd32,
                                                    const uint8_t* __restrict__ kind, const int32_t* __restrict__ wgt,
-                                                   const int32_t* __restrict__ oddsz, int32_t* __restrict__ key) {
+                                                   const int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
+                                                   const Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: no chain walk
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -994,7 +997,9 @@ __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __
 // Depth of every finite vertex (outputs only): the number of vertices on its
 // play before the sink, the sum of the walk lengths along its g-chain.
 __global__ void __launch_bounds__(kBlock) k_depth(int32_t n, const uint64_t* __restrict__ gd,
-                                                  const uint8_t* __restrict__ kind, int32_t* __restrict__ depth) {
+                                                  const uint8_t* __restrict__ kind, int32_t* __restrict__ depth,
+                                                  const Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: no chain walk
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int32_t dep = -1;
         if (kind[v] & kKFin) {
@@ -1130,10 +1135,242 @@ __global__ void __launch_bounds__(kBlock) k_reset_odd(int32_t n, const OffT* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Loop iterations without ranks. Switching (Section 3, "Switching rules")
+// only compares the valuations of a vertex's successors with each other, so
+// the loop does not need the position of every valuation in the order: two
+// finite valuations are compared directly on the g-forest. Walk both g-chains
+// upwards, always advancing the smaller id, until they meet at their lowest
+// common g-ancestor (at the latest the game's sink slot). The largest vertex
+// of the symmetric difference of the two plays is the larger of the last two
+// vertices passed below the meeting point; its side wins for Even when its
+// priority is even. TOP valuations are above every finite one and equal to
+// each other. The dense ranks, depths and classes of the outputs come from a
+// full valuation after the loop.
+
+// After k_classify, bit 31 of a g-word marks a TOP vertex (its play ends in
+// a cycle); finite words are unchanged (bit 30: g(v) is the game's sink slot).
+constexpr uint32_t kG32Top = 0x80000000u;
+// k_classify also writes one "top word" per vertex: bit 31 = TOP; for a finite
+// vertex bits 0..29 = its top, the last vertex of its g-chain below the sink
+// slot (a child of the sink in the g-forest), and bit 30 = that top's priority
+// is odd.
+constexpr uint32_t kTopOdd = 0x40000000u;
+__device__ inline int32_t top_id(uint32_t t) { return (int32_t)(t & 0x3fffffffu); }
+
+// Class and top of every vertex from its g-chain: a chain that ends at a
+// "none" vertex (above its whole infinite future) or passes a vertex already
+// marked TOP is TOP, and its g-word gets bit 31; a chain that reaches the sink
+// is finite, its top being the chain's last vertex. g-words change only by
+// gaining bit 31 on TOP vertices, and a walker that reads either the old or
+// the new word of a TOP vertex stops there with the same answer, so the
+// in-place marks are race-free shortcuts. A cycle maximum (a none vertex whose
+// pointer is itself) with an odd priority counts toward its game's odd cycles
+// (sigma not admissible).
+__global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags,
+                                                     uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
+                                                     GameState* gst, const Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], x[kIlp];
+        uint32_t w0[kIlp];
+        bool act[kIlp], top[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
+            w0[j] = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
+            top[j] = g32_none(w0[j]);
+            x[j] = g32_sink(w0[j]) ? v[j] : g32_ptr(w0[j]);  // a child of the sink is its own top
+            act[j] = !(w0[j] & (kG32None | kG32Sink));
+            if (v[j] < n && g32_none(w0[j]) && x[j] == v[j] && (flags[v[j]] & kPriOdd))
+                atomicAdd(&gst[vgame ? vgame[v[j]] : 0].nodd, 1);
+        }
+        for (;;) {
+            bool any = false;
+            uint32_t wx[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    if (wx[j] & kG32Top) {  // a none vertex, or one already marked TOP
+                        top[j] = true;
+                        act[j] = false;
+                    } else if (g32_sink(wx[j])) {  // x is the top
+                        act[j] = false;
+                    } else {
+                        const int32_t nx = g32_ptr(wx[j]);
+                        act[j] = nx > x[j];  // g-chains rise (a guard, never false here)
+                        x[j] = nx;
+                    }
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+        uint8_t fx[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (v[j] >= n) continue;
+            if (top[j] && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
+            topw[v[j]] = top[j] ? kG32Top : ((fx[j] & kPriOdd) ? kTopOdd : 0u) | (uint32_t)x[j];
+        }
+    }
+}
+
+// Compares the valuations of two finite vertices u and w of one game with the
+// same top: walk both g-chains (words wu, ww) upwards, always advancing the
+// smaller id, until they meet (at the top at the latest). The larger of the
+// last two vertices passed below the meeting point is the largest vertex of
+// the symmetric difference of the two plays; its side is better for Even
+// when its priority is even. Returns > 0 if Val(u) is better for Even, < 0 if
+// worse, 0 if u == w. g(x) > x for every vertex below the top, so each step
+// raises a or b.
+__device__ inline int cmp_walk(int32_t u, int32_t w, const uint32_t* __restrict__ gd32,
+                               const uint8_t* __restrict__ flags) {
+    int32_t a = u, b = w, pa = -1, pb = -1;
+    uint32_t wa = 0, wb = 0;
+    if (a != b) {
+        wa = gd32[a];
+        wb = gd32[b];
+    }
+    while (a != b) {
+        if (a < b) {
+            pa = a;
+            a = g32_ptr(wa);
+            if (a <= pa) return 0;  // g-chains rise (a guard that keeps every walk finite; never taken)
+            wa = gd32[a];
+        } else {
+            pb = b;
+            b = g32_ptr(wb);
+            if (b <= pb) return 0;
+            wb = gd32[b];
+        }
+    }
+    if (pa == pb) return 0;  // u == w
+    const bool u_side = pa > pb;
+    const bool even = !(flags[u_side ? pa : pb] & kPriOdd);
+    return u_side == even ? 1 : -1;
+}
+
+// Order of the valuations of u and w (vertices of one game, with their top
+// words tu, tw): > 0 if Val(u) is better for Even than Val(w), < 0 if worse,
+// 0 if equal. TOP is above every finite valuation and equal to TOP. Finite
+// plays with different tops differ above everything else at the larger top,
+// which decides by its parity; with the same top the chains are walked.
+__device__ inline int cmp_val(int32_t u, uint32_t tu, int32_t w, uint32_t tw, const uint32_t* __restrict__ gd32,
+                              const uint8_t* __restrict__ flags) {
+    const int xu = (tu & kG32Top) ? 1 : 0, xw = (tw & kG32Top) ? 1 : 0;
+    if (xu | xw) return xu - xw;
+    const int32_t hu = top_id(tu), hw = top_id(tw);
+    if (hu != hw) {
+        const bool u_side = hu > hw;
+        const bool even = !((u_side ? tu : tw) & kTopOdd);
+        return u_side == even ? 1 : -1;
+    }
+    return cmp_walk(u, w, gd32, flags);
+}
+
+// Against the sink's empty valuation: the top of a finite play is its largest
+// vertex, so Val(u) is better for Even exactly when that top is even.
+__device__ inline int cmp_sink(uint32_t tu) {
+    if (tu & kG32Top) return 1;
+    return (tu & kTopOdd) ? -1 : 1;
+}
+
+// K3 with comparisons: as k_switch (one thread per vertex of the switching
+// player, the first minimiser for Odd, the sink first and then the first
+// maximiser for Even, a switch only when strictly better), with the best
+// successor kept by comparing valuations. Two valuations are equal only when
+// both are TOP, so Odd switches when its best successor differs from the
+// current one and is finite, Even when they differ and the current one is not
+// TOP (the best one is then at least as good as TOP only if equal to it).
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_switch_cmp(int32_t n, int player, const OffT* __restrict__ off,
+                                                       const int32_t* __restrict__ tgt,
+                                                       const uint8_t* __restrict__ flags,
+                                                       const uint32_t* __restrict__ gd32,
+                                                       const uint32_t* __restrict__ topw,
+                                                       const int32_t* __restrict__ vgame,
+                                                       const int32_t* __restrict__ gsink, int32_t sink0,
+                                                       GameState* gst, int32_t* strat, Counters* cnt) {
+    if (cnt->err) return;  // unfinished jumping: no comparison walk
+    if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
+        const GameState st = gst[0];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
+    }
+    int32_t nsw = 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        if ((f & kSinkSlot) || (int)(f & kOwnerOdd) != player) continue;
+        const int32_t gi = vgame ? vgame[v] : 0;
+        if (vgame) {
+            const GameState st = gst[gi];
+            if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) continue;
+        }
+        const int64_t e0 = off[v], e1 = off[v + 1];
+        const int32_t cur = strat[v];
+        const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : -1;
+        int32_t best = sk;  // Even: the sink first; Odd: none yet
+        uint32_t tbest = 0;
+        bool cur_top = false;
+        for (int64_t e = e0; e < e1; e += 4) {
+            int32_t t[4];
+            uint32_t tt[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? tgt[e + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tt[j] = t[j] >= 0 ? topw[t[j]] : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (t[j] < 0) continue;
+                if (t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
+                bool take;
+                if (player == 1) take = best < 0 || cmp_val(t[j], tt[j], best, tbest, gd32, flags) < 0;
+                else take = (best == sk ? cmp_sink(tt[j]) : cmp_val(t[j], tt[j], best, tbest, gd32, flags)) > 0;
+                if (take) {
+                    best = t[j];
+                    tbest = tt[j];
+                }
+            }
+        }
+        const bool sw = best != cur && (player == 0 ? !cur_top : !(tbest & kG32Top));
+        if (sw) {
+            strat[v] = best;
+            ++nsw;
+            if (vgame) {  // one count per group of lanes of the same game
+                cg::coalesced_group swg = cg::coalesced_threads();
+                cg::coalesced_group same = cg::labeled_partition(swg, gi);
+                if (same.thread_rank() == 0)
+                    atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+            }
+        }
+    }
+    block_add(nsw, &cnt->n_switch);
+    if (!vgame) {  // one game: the block totals are the game's
+        __shared__ int32_t tot;
+        if (threadIdx.x == 0) tot = 0;
+        __syncthreads();
+        int32_t x = nsw;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&tot, x);
+        __syncthreads();
+        if (threadIdx.x == 0 && tot) atomicAdd(player ? &gst[0].sw_odd : &gst[0].sw_even, tot);
+    }
+}
+
 }  // namespace
 
 const char* const kKernelNames[KID_COUNT] = {"walk",     "jump",      "chain1", "child_scan", "scatter",
-                                              "siblings", "sink_scan", "chain2", "switch_odd", "switch_even"};
+                                              "siblings", "sink_scan", "chain2", "switch_odd", "switch_even",
+                                              "classify"};
 
 void prof_begin(pg_game* g, int id) {
     if (g->ctx->timing) cudaEventRecord(g->kev[2 * id], g->ctx->stream);
@@ -1301,7 +1538,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         prof_end(g, KID_SINKSCAN, single ? 3 : 4);
     }
     prof_begin(g, KID_CHAIN2);
-    k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key);
+    k_chain2<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->wgt, g->oddsz, g->key, c);
     prof_end(g, KID_CHAIN2, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
@@ -1310,7 +1547,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
 pg_status enqueue_depth(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     ctx->launches += 1;
-    k_depth<<<grid_for(g->n), kBlock, 0, ctx->stream>>>(g->n, g->gd, g->kind, g->depth);
+    k_depth<<<grid_for(g->n), kBlock, 0, ctx->stream>>>(g->n, g->gd, g->kind, g->depth, g->cnt);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
@@ -1356,6 +1593,60 @@ pg_status enqueue_reset(pg_game* g) {
                                                                g->strat);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
+}
+
+bool loop_compares(const pg_game* g) { return !g->cv && !g->ctx->loop_ranks; }
+
+pg_status enqueue_valuation_cmp(pg_game* g) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    int32_t n = g->n;
+    Counters* c = g->cnt;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
+    prof_begin(g, KID_WALK);
+    k_walk<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd,
+                                                    g->gd32, g->plist, g->sz, g->oddsz, c, &c->n_pending);
+    prof_end(g, KID_WALK, 1);
+    {
+        int32_t cap = 64;
+        for (int64_t x = n; x > 1; x >>= 1) cap += 2;
+        void* args[] = {(void*)&g->plist, (void*)&g->gd,    (void*)&g->gd32, (void*)&g->vgame,
+                        (void*)&g->gsink, (void*)&g->sink0, (void*)&c,       (void*)&cap};
+        prof_begin(g, KID_JUMP);
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
+        prof_end(g, KID_JUMP, 1);
+    }
+    prof_begin(g, KID_CLASSIFY);
+    // the top words live in the chain-weight array, which only a full valuation uses
+    k_classify<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame, g->gst, c);
+    prof_end(g, KID_CLASSIFY, 1);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_switch_cmp(pg_game* g, int player) {
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
+    int kid = player ? KID_SWITCH_ODD : KID_SWITCH_EVEN;
+    prof_begin(g, kid);
+    if (g->off64)
+        k_switch_cmp<int64_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off64, g->tgt, g->flags, g->gd32,
+                                                                (const uint32_t*)g->wgt, g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+    else
+        k_switch_cmp<int32_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->gd32,
+                                                                (const uint32_t*)g->wgt, g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+    prof_end(g, kid, 1);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status finish_loop(pg_game* g) {
+    if (!g->last_cmp) return PG_OK;
+    pg_status st = enqueue_valuation(g, false);
+    if (!st) st = sync_counters(g);
+    if (!st) g->last_cmp = false;
+    return st;
 }
 
 pg_status sync_counters(pg_game* g) {

@@ -480,13 +480,14 @@ void worker_main(pg_server* sv) {
             sv->stats.loop_ms += (t_col - t_loop) / 1e3;
         }
         if (!any_done) continue;
-        if (any_timeout) {  // results describe the profile being returned
+        if (any_timeout || sv->B->last_cmp) {  // results describe the profile being returned (full valuation)
             st = enqueue_valuation(sv->B, false);
             if (!st) st = sync_counters(sv->B);
             if (st) {
                 set_fatal(sv, st, ctx);
                 return;
             }
+            sv->B->last_cmp = false;
         }
         st = enqueue_depth(sv->B);  // once for every finished game of this round
         if (st) {

@@ -114,6 +114,7 @@ def lib():
     L.pg_valuate.argtypes = [P, P, P, P, I32, C.POINTER(pg_valuation)]
     L.pg_set_timing.argtypes = [P, I32]
     L.pg_set_graphs.argtypes = [P, I32]
+    L.pg_set_loop_ranks.argtypes = [P, I32]
     L.pg_release_cached_memory.argtypes = [C.c_int]
     L.pg_last_loop.argtypes = [P, C.POINTER(I32), C.POINTER(I64)]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -133,7 +134,7 @@ def lib():
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
                  "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters", "pg_best_response_bf"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -465,6 +466,10 @@ def pg_set_timing(ctx, enable):
 
 def pg_set_graphs(ctx, enable):
     _check(ctx, lib().pg_set_graphs(ctx, 1 if enable else 0), "pg_set_graphs")
+
+
+def pg_set_loop_ranks(ctx, enable):
+    _check(ctx, lib().pg_set_loop_ranks(ctx, 1 if enable else 0), "pg_set_loop_ranks")
 
 
 def pg_release_cached_memory(device=0):
