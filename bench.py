@@ -454,12 +454,18 @@ SERVE = {
 def serve_measure(name, seconds, cpu_budget=0):
     """Submits arrivals of a Poisson process for ``seconds`` from one thread,
     polls results from another, then solves the pool one game at a time
-    (pg_load_csr + pg_solve from host arrays) for comparison."""
+    (pg_load_csr + pg_solve from host arrays) for comparison. With several
+    ranks the stream shards by arrival (shard.stream_assign: each arrival to
+    the rank with the least work submitted so far, decided by every rank alone);
+    each rank serves its arrivals on its own GPU, and rank 0 reports all games
+    over the slowest rank's time. The queue of waiting games is sampled every
+    half second to show whether it stays bounded."""
     import threading
 
     import torch
 
-    from paper_1705_02313_gb300 import gen, pg
+    from paper_1705_02313_gb300 import gen, pg, shard
+    ws, rank, _ = dist_env()
     cfg = SERVE[name]
     t0 = time.perf_counter()
     vb, eb, off, tgt, own, pri = gen.native_batch(cfg["pool"], cfg["lo"], cfg["hi"], cfg["dmin"], cfg["dmax"])
@@ -472,67 +478,105 @@ def serve_measure(name, seconds, cpu_budget=0):
     gaps = rng.exponential(1.0 / cfg["rate"], size=int(cfg["rate"] * seconds * 2) + 16)
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < seconds]
-    sv = pg.pg_server_create(0)
+    owner = shard.stream_assign(np.diff(vb)[np.arange(arrivals.size) % P], ws)
+    mine = np.nonzero(owner == rank)[0]
+    sv = pg.pg_server_create(torch.cuda.current_device())
     done = {}
     submit_err = []
+    queue_trace = []  # (seconds since start, games waiting, games submitted, games completed)
+    stop = threading.Event()
 
     def submitter():
         start = time.perf_counter()
         try:
-            for j, ta in enumerate(arrivals):
-                d = ta - (time.perf_counter() - start)
+            for j in mine:
+                d = arrivals[j] - (time.perf_counter() - start)
                 if d > 0:
                     time.sleep(d)
                 n, m, o, t, w, p = pool[j % P]
-                pg.pg_server_submit(sv, n, m, o, t, w, p, tag=j)
+                pg.pg_server_submit(sv, n, m, o, t, w, p, tag=int(j))
         except Exception as e:  # reported in the result
             submit_err.append(repr(e))
 
+    def sampler():
+        while not stop.wait(0.5):
+            st = pg.pg_server_get_stats(sv)
+            queue_trace.append((round(time.perf_counter() - t_start, 2), int(st["queued"]), int(st["submitted"]),
+                                int(st["completed"])))
+
+    shard.barrier()
     th = threading.Thread(target=submitter)
+    ts = threading.Thread(target=sampler, daemon=True)
     t_start = time.perf_counter()
     th.start()
+    ts.start()
     limit = seconds + 120.0
-    while len(done) < len(arrivals) and time.perf_counter() - t_start < limit:
+    while len(done) < len(mine) and time.perf_counter() - t_start < limit:
         for r in pg.pg_server_poll(sv, 256, 50):
             done[r["tag"]] = (r, time.perf_counter())
             pg.pg_server_fetch(sv, r["tag"], r["n"], r["k"], keep=False)
     th.join()
+    stop.set()
     t_last = max((x[1] for x in done.values()), default=time.perf_counter())
     stats = pg.pg_server_get_stats(sv)
     pg.pg_server_destroy(sv)
-    lat = np.array([x[0]["latency_us"] for x in done.values()]) / 1e3
-    qus = np.array([x[0]["queue_us"] for x in done.values()]) / 1e3
-    ok = sum(1 for x in done.values() if x[0]["status"] == pg.PG_OK)
-    served = len(done) / (t_last - t_start) if done else 0.0
-    # one at a time over the pool (host arrays, as submitted)
-    ctx = pg.pg_ctx_create(0)
-    t0 = time.perf_counter()
-    for (n, m, o, t, w, p) in pool:
-        g = pg.pg_load_csr(ctx, n, m, o, t, w, p)
-        try:
-            pg.pg_solve(ctx, g, win=np.empty(n, np.uint8))
-        finally:
-            pg.pg_game_free(g)
-    t_single = time.perf_counter() - t0
-    pg.pg_ctx_destroy(ctx)
+    lat_l = [x[0]["latency_us"] / 1e3 for x in done.values()]
+    qus_l = [x[0]["queue_us"] / 1e3 for x in done.values()]
+    ok_l = sum(1 for x in done.values() if x[0]["status"] == pg.PG_OK)
+    # served over the second half of the window: completions per second against arrivals per second
+    half = [x[1] - t_start for x in done.values() if seconds / 2 <= x[1] - t_start <= seconds]
+    lat = np.concatenate([np.asarray(x, dtype=np.float64) for x in shard.gather_to_all(lat_l)])
+    qus = np.concatenate([np.asarray(x, dtype=np.float64) for x in shard.gather_to_all(qus_l)])
+    ok = int(shard.sum_over_ranks(ok_l))
+    completed = int(shard.sum_over_ranks(len(done)))
+    span = shard.max_over_ranks(t_last - t_start)
+    served = completed / span if completed else 0.0
+    served_2nd_half = shard.sum_over_ranks(len(half)) / (seconds / 2)
+    traces = shard.gather_to_all(queue_trace)
+    qmax = max((q for tr in traces for (_, q, _, _) in tr), default=0)
+    q_end = sum(tr[-1][1] for tr in traces if tr)
+    q_mid = sum(min(tr, key=lambda e: abs(e[0] - seconds / 2))[1] for tr in traces if tr)
+    # one at a time over the pool (host arrays, as submitted), on rank 0's GPU
+    t_single = None
+    if rank == 0:
+        ctx = pg.pg_ctx_create(torch.cuda.current_device())
+        t0 = time.perf_counter()
+        for (n, m, o, t, w, p) in pool:
+            g = pg.pg_load_csr(ctx, n, m, o, t, w, p)
+            try:
+                pg.pg_solve(ctx, g, win=np.empty(n, np.uint8))
+            finally:
+                pg.pg_game_free(g)
+        t_single = time.perf_counter() - t0
+        pg.pg_ctx_destroy(ctx)
     torch.cuda.synchronize()
     cpu = None
-    if cpu_budget > 0:
+    if cpu_budget > 0 and rank == 0:
         c = cpu_batch(P, cfg["lo"], cfg["hi"], cfg["dmin"], cfg["dmax"], cpu_budget)
         cpu = {"value": c["games"] / c["seconds"], "unit": "games/s", "cores": c["cores"], "kind": "oracle",
                "sample": "games 0..%d of the pool (%d vertices), one game per process on %d processes, %.1f s wall "
                          "(%.1f s of single-thread solves)"
                          % (c["games"] - 1, c["vertices"], c["cores"], c["seconds"], c["solve_seconds"])}
+    offered = len(arrivals) / seconds
     return {"workload": name, "description": cfg["desc"], "seconds": seconds, "arrivals": int(len(arrivals)),
-            "completed": len(done), "ok": ok, "metric": "served games/s and latency", "unit": "games/s",
-            "served_games_per_s": served, "offered_games_per_s": len(arrivals) / seconds,
+            "ranks": ws, "arrivals_per_rank": [int(x) for x in np.bincount(owner, minlength=ws)],
+            "completed": completed, "ok": ok, "metric": "served games/s and latency", "unit": "games/s",
+            "served_games_per_s": served, "offered_games_per_s": offered,
+            "served_games_per_s_second_half": served_2nd_half,
             "latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
             "latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
             "queue_ms_p50": float(np.percentile(qus, 50)) if qus.size else None,
-            "one_at_a_time_games_per_s": P / t_single, "pool_games": P,
+            "queue": {"waiting_max": int(qmax), "waiting_at_half": int(q_mid), "waiting_at_end": int(q_end),
+                      "bounded": bool(served_2nd_half >= 0.95 * offered),
+                      "trace_rank0": queue_trace[::4],
+                      "note": "games submitted and not yet admitted, sampled every 0.5 s (trace: every 2 s: "
+                              "seconds, waiting, submitted, completed); bounded = completions in the second half "
+                              "of the window keep up with arrivals (>= 95%)"},
+            "one_at_a_time_games_per_s": (P / t_single) if t_single else None, "pool_games": P,
             "pool_vertices": int(vb[-1]), "pool_edges": int(eb[-1]), "generate_s": t_gen,
             "server": stats, "submit_errors": submit_err, "cpu_baseline": cpu,
-            "timing": "wall clock; latency from submission to result, measured by the server"}
+            "timing": "wall clock; latency from submission to result, measured by the server; with several ranks, "
+                      "all ranks' games over the slowest rank's span"}
 
 
 # ---------------------------------------------------------------------------
@@ -815,8 +859,10 @@ def run_ours(args):
         b = batch_measure(args.batch, 0 if args.no_cpu_baseline else args.batch_cpu_vertices)
         if rank == 0:
             line["batch"] = b
-    if rank == 0 and args.serve > 0:
-        line["serve"] = serve_measure("serve-200", args.serve, 0 if args.no_cpu_baseline else args.serve_cpu_vertices)
+    if args.serve > 0:  # every rank serves its share of the stream
+        sres = serve_measure("serve-200", args.serve, 0 if args.no_cpu_baseline else args.serve_cpu_vertices)
+        if rank == 0:
+            line["serve"] = sres
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_sample(game, args.cpu_iters)
         line["cpu_baseline"] = {"value": r["edges"] * r["iters"] / r["seconds"], "unit": UNIT, "cores": 1,

@@ -268,6 +268,8 @@ typedef struct {
     int32_t max_games;     /* resident games; 0 = 4096 */
     int32_t round_iters;   /* iterations per round (admission points); 0 = 8 */
     int64_t max_inner;     /* per-game iteration cap; 0 = 64 (largest resident n' + 64) */
+    int32_t wide_offsets;  /* 1: the resident layout keeps 64-bit edge offsets at any size (as
+                              pg_set_wide_offsets); 0: only when it holds 2^31 or more edges */
 } pg_server_opts;
 
 /* One finished game, as reported by pg_server_poll. */
@@ -381,6 +383,12 @@ pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuatio
  * synchronises once per iteration. Both give identical results. The paper has
  * no counterpart (it concerns launching work on the device only). */
 pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
+/* Edge offsets of the packed layout of pg_solve_batch: 32-bit while the batch
+ * holds fewer than 2^31 edges, 64-bit beyond. enable = 1 takes 64-bit offsets
+ * at any size (the layout of the largest batches, e.g. to check it on small
+ * ones); results are identical. The paper has no counterpart. */
+pg_status pg_set_wide_offsets(pg_ctx *ctx, int32_t enable);
+
 /* What each iteration of the loops of pg_solve / pg_best_response /
  * pg_solve_batch / the server computes for switching (distinct priorities;
  * count-vector games always rank). By default (enable = 0) an iteration builds

@@ -521,6 +521,12 @@ pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
     return PG_OK;
 }
 
+pg_status pg_set_wide_offsets(pg_ctx* ctx, int32_t enable) {
+    if (!ctx) return PG_EINVAL;
+    ctx->wide_offsets = enable != 0;
+    return PG_OK;
+}
+
 pg_status pg_set_loop_ranks(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;
     ctx->loop_ranks = enable != 0;

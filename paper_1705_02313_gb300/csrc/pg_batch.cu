@@ -81,7 +81,7 @@ pg_status pack_games(pg_ctx* ctx, pg_game** games, int32_t ngames, pg_game** out
     g->n0 = n0;
     g->k = (int32_t)K;
     for (int32_t i = 0; i < ngames; ++i) g->m0 += games[i]->m0;
-    const bool wide = M > INT32_MAX - 1;
+    const bool wide = ctx->wide_offsets || M > INT32_MAX - 1;
     auto A = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes, ctx->stream); };
 #define PK_TRY(expr)                                                 \
     do {                                                             \

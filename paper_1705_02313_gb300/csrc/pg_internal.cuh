@@ -127,6 +127,7 @@ struct pg_ctx {
     bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
     bool graphs = true;         // run the iteration loop as one CUDA graph with a device-side condition
     bool loop_ranks = false;    // loop iterations rank every valuation (else they only compare them)
+    bool wide_offsets = false;  // batches take 64-bit edge offsets at any size (else from 2^31 edges)
     cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
 

@@ -279,6 +279,118 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
     }
 }
 
+// Compare-mode K1 (loop iterations that compare valuations): the same walks
+// and jumps with 4-byte g-words only. A word with both the none and the sink
+// bit set is pending: its low bits are a jump pointer (every vertex strictly
+// between v and it on the play is below v, and so is the pointer).
+constexpr uint32_t kG32Pend = kG32None | kG32Sink;
+__device__ inline bool g32_pending(uint32_t w) { return (w & kG32Pend) == kG32Pend; }
+
+template <uint32_t cap>
+__global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
+                                                     const uint8_t* __restrict__ flags,
+                                                     const int32_t* __restrict__ vgame,
+                                                     const int32_t* __restrict__ gsink, int32_t sink0,
+                                                     uint32_t* __restrict__ gd32, int32_t* __restrict__ more,
+                                                     int32_t* more_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+         tile += nwarps) {
+        int32_t v[kIlp], x[kIlp];
+        uint32_t d[kIlp];
+        bool act[kIlp], slotid[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
+            d[j] = 1;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < cap;
+        for (;;) {
+            bool any = false;
+            int32_t nx[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (act[j]) {
+                    x[j] = nx[j];
+                    ++d[j];
+                    act[j] = x[j] < v[j] && d[j] < cap;
+                }
+                any |= act[j];
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            bool pend = false;
+            if (v[j] < n) {
+                uint32_t w;
+                if (slotid[j]) w = kG32Sink | (uint32_t)v[j];  // a sink slot: inert
+                else if (x[j] > v[j]) w = (x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink : 0u) | (uint32_t)x[j];
+                else if (x[j] == v[j]) w = kG32None | (uint32_t)v[j];  // v is its cycle's maximum
+                else {
+                    w = kG32Pend | (uint32_t)x[j];
+                    pend = true;
+                }
+                gd32[v[j]] = w;
+            }
+            int32_t slot = warp_append(pend, more_count);
+            if (pend) more[slot] = v[j];
+        }
+    }
+}
+
+// Pointer jumping on the 4-byte words for the walks that ran out of steps,
+// all rounds in one cooperative launch (as k_jump_coop, without walk lengths).
+__global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restrict__ plist, uint32_t* gd32,
+                                                        const int32_t* __restrict__ vgame,
+                                                        const int32_t* __restrict__ gsink, int32_t sink0,
+                                                        Counters* cnt, int32_t cap) {
+    const int32_t np = cnt->n_pending;
+    if (np == 0) return;
+    for (int32_t r = 0;; ++r) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt->left[(r + 1) % 3] = 0;
+        int32_t left = 0;
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+            const int32_t v = plist[i];
+            const uint32_t w = __ldcg(gd32 + v);
+            if (!g32_pending(w)) continue;
+            const int32_t x = g32_ptr(w);
+            const uint32_t wx = __ldcg(gd32 + x);
+            uint32_t nw;
+            if (g32_none(wx) && !g32_pending(wx)) {
+                // x is above its whole future and below v: so is v (same cycle)
+                nw = kG32None | (uint32_t)g32_ptr(wx);
+            } else {
+                const int32_t y = g32_ptr(wx);
+                if (y > v) nw = (y == sink_of(v, vgame, gsink, sink0) ? kG32Sink : 0u) | (uint32_t)y;
+                else if (y == v) nw = kG32None | (uint32_t)v;
+                else {
+                    nw = kG32Pend | (uint32_t)y;
+                    ++left;
+                }
+            }
+            __stcg(gd32 + v, nw);
+        }
+        block_add(left, &cnt->left[r % 3]);
+        if (!grid_sync(cnt)) return;
+        int32_t rem = *(volatile int32_t*)&cnt->left[r % 3];
+        if (rem == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) cnt->jump_rounds = r + 1;
+            return;
+        }
+        if (r + 1 >= cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cnt->err, kErrJumpRounds);
+            return;
+        }
+    }
+}
+
 // Size additions near the roots of deep g-trees. Every vertex of a large
 // g-tree has the same few vertices near the root among its ancestors, and one
 // global atomic per vertex on each of them would serialise (an n-long chain: n
@@ -1447,7 +1559,9 @@ pg_status coop_blocks_for(pg_ctx* ctx, int* out) {
     PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jump_coop, kBlock, 0));
     PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_idscan_coop, kBlock, 0));
-    *out = sms * std::max(1, std::min(std::min(a, b), 4));
+    int c = 0;
+    PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_jump32_coop, kBlock, 0));
+    *out = sms * std::max(1, std::min(std::min(std::min(a, b), c), 4));
     return PG_OK;
 }
 
@@ -1604,16 +1718,16 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     Counters* c = g->cnt;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd,
-                                                    g->gd32, g->plist, g->sz, g->oddsz, c, &c->n_pending);
+    k_walk_cmp<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32,
+                                                        g->plist, &c->n_pending);
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
-        void* args[] = {(void*)&g->plist, (void*)&g->gd,    (void*)&g->gd32, (void*)&g->vgame,
-                        (void*)&g->gsink, (void*)&g->sink0, (void*)&c,       (void*)&cap};
+        void* args[] = {(void*)&g->plist, (void*)&g->gd32, (void*)&g->vgame, (void*)&g->gsink,
+                        (void*)&g->sink0, (void*)&c,       (void*)&cap};
         prof_begin(g, KID_JUMP);
-        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump32_coop, g->coop_blocks, kBlock, args, 0, s));
         prof_end(g, KID_JUMP, 1);
     }
     prof_begin(g, KID_CLASSIFY);

@@ -156,7 +156,7 @@ pg_status alloc_batch(pg_server* sv) {
     sv->B = g;
     auto A = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes, ctx->stream); };
     const int64_t N = sv->capN, M = sv->capM;
-    if (M > INT32_MAX - 1) PG_CUDA_TRY(ctx, A((void**)&g->off64, sizeof(int64_t) * (N + 1)));
+    if (sv->opts.wide_offsets || M > INT32_MAX - 1) PG_CUDA_TRY(ctx, A((void**)&g->off64, sizeof(int64_t) * (N + 1)));
     else PG_CUDA_TRY(ctx, A((void**)&g->off, sizeof(int32_t) * (N + 1)));
     PG_CUDA_TRY(ctx, A((void**)&g->tgt, sizeof(int32_t) * M));
     PG_CUDA_TRY(ctx, A((void**)&g->flags, N));

@@ -60,7 +60,7 @@ class pg_result_batch(C.Structure):
 
 class pg_server_opts(C.Structure):
     _fields_ = [("max_vertices", C.c_int64), ("max_edges", C.c_int64), ("max_games", C.c_int32),
-                ("round_iters", C.c_int32), ("max_inner", C.c_int64)]
+                ("round_iters", C.c_int32), ("max_inner", C.c_int64), ("wide_offsets", C.c_int32)]
 
 
 class pg_served(C.Structure):
@@ -115,6 +115,7 @@ def lib():
     L.pg_set_timing.argtypes = [P, I32]
     L.pg_set_graphs.argtypes = [P, I32]
     L.pg_set_loop_ranks.argtypes = [P, I32]
+    L.pg_set_wide_offsets.argtypes = [P, I32]
     L.pg_release_cached_memory.argtypes = [C.c_int]
     L.pg_last_loop.argtypes = [P, C.POINTER(I32), C.POINTER(I64)]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -134,7 +135,7 @@ def lib():
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_set_wide_offsets", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
                  "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters", "pg_best_response_bf"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -376,8 +377,10 @@ def pack_games(games):
     return vtx_base, edge_base, offsets, targets, owner, pri
 
 
-def pg_server_create(device=0, max_vertices=0, max_edges=0, max_games=0, round_iters=0, max_inner=0):
-    opts = pg_server_opts(int(max_vertices), int(max_edges), int(max_games), int(round_iters), int(max_inner))
+def pg_server_create(device=0, max_vertices=0, max_edges=0, max_games=0, round_iters=0, max_inner=0,
+                     wide_offsets=False):
+    opts = pg_server_opts(int(max_vertices), int(max_edges), int(max_games), int(round_iters), int(max_inner),
+                          1 if wide_offsets else 0)
     sv = C.c_void_p()
     rc = lib().pg_server_create(int(device), C.byref(opts), C.byref(sv))
     if rc != PG_OK:
@@ -466,6 +469,10 @@ def pg_set_timing(ctx, enable):
 
 def pg_set_graphs(ctx, enable):
     _check(ctx, lib().pg_set_graphs(ctx, 1 if enable else 0), "pg_set_graphs")
+
+
+def pg_set_wide_offsets(ctx, enable):
+    _check(ctx, lib().pg_set_wide_offsets(ctx, 1 if enable else 0), "pg_set_wide_offsets")
 
 
 def pg_set_loop_ranks(ctx, enable):

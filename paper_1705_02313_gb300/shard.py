@@ -4,9 +4,11 @@ The games of a batch or of a request stream are independent problems, so
 they shard with no collective on the data path: each rank loads and solves
 its own games. Collectives are used only around that, to agree on timings
 (the slowest rank's time) and to bring results or counts to one rank for
-reporting. Games are assigned largest first to the rank with the least work
-so far (greedy LPT), with the vertex count as the work of a game; ties go to
-the lower rank, so every rank computes the same assignment on its own.
+reporting. The games of a batch are assigned largest first to the rank with
+the least work so far (greedy LPT), with the vertex count as the work of a
+game; the arrivals of a stream go, in arrival order, to the rank with the
+least work submitted so far. Ties go to the lower rank, so every rank
+computes the same assignment on its own.
 """
 from __future__ import annotations
 
@@ -33,6 +35,24 @@ def lpt_assign(weights, world):
 def shard_of(weights, world, rank):
     """The games of ``rank`` (ascending indices)."""
     return lpt_assign(weights, world)[rank]
+
+
+def stream_assign(weights, world):
+    """Owner rank of each arrival of a request stream, in arrival order: each
+    arrival goes to the rank with the least work submitted so far (its
+    vertices), ties to the lower rank. Unlike lpt_assign it looks at no later
+    arrival, so a rank can decide on each request as it comes; every rank
+    that sees the same arrivals computes the same owners, with no message."""
+    w = np.asarray(weights, dtype=np.int64)
+    if world < 1:
+        raise ValueError("world must be at least 1")
+    heap = [(0, r) for r in range(world)]
+    owner = np.empty(w.size, dtype=np.int64)
+    for i in range(w.size):
+        load, r = heapq.heappop(heap)
+        owner[i] = r
+        heapq.heappush(heap, (load + int(w[i]), r))
+    return owner
 
 
 def _dist():

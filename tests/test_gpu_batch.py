@@ -81,6 +81,32 @@ def test_batch_matches_oracle_per_game(pg, ctx):
     assert res["iterations"] == res["inner"].max()
 
 
+@pytest.mark.parametrize("loop_ranks", [0, 1])
+def test_batch_with_wide_offsets_matches_oracle_per_game(pg, ctx, loop_ranks):
+    """The layout of batches of 2^31 or more edges (64-bit edge offsets: the
+    packing, the initial profile and both switching kernels on int64 offsets),
+    forced on a small batch with a few larger games, in both loop modes."""
+    games = mixed_games(16, 23) + [gen.random_game(150_000, 2, 6, gen.batch_seed(9001)),
+                                   gen.ladder_game(60_000, seed=9002)]
+    pg.pg_set_wide_offsets(ctx, 1)
+    pg.pg_set_loop_ranks(ctx, loop_ranks)
+    try:
+        vb, res, out = run_batch(pg, ctx, games, device=True)
+    finally:
+        pg.pg_set_wide_offsets(ctx, 0)
+        pg.pg_set_loop_ranks(ctx, 0)
+    assert res["rc"] == pg.PG_OK and (res["status"] == 0).all()
+    db = res["dummy_base"]
+    for i, g in enumerate(games):
+        gp, r, want = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
+        sl = slice(int(vb[i]), int(vb[i + 1]))
+        for k in KEYS:
+            assert np.array_equal(out[k][sl], np.asarray(want[k])), (i, g.n, k)
+        assert (res["major"][i], res["inner"][i]) == (want["major"], want["inner"]), i
+        dsig = (r["strat"][gp["n_orig"]:] != gp["n"]).astype(np.int8)
+        assert np.array_equal(out["dummy_sigma"][int(db[i]):int(db[i + 1])], dsig), i
+
+
 def test_batch_equals_single_solves_device_inputs(pg, ctx):
     games = mixed_games(9, 11)
     vb, res, out = run_batch(pg, ctx, games, device=True)

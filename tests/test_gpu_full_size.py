@@ -1,8 +1,16 @@
 """Parity at the full size of the benchmark's workloads: the 10,000,000-vertex
-random game (out-degree U[2,5], owners p = 0.5, permuted priorities, seed 0)
-and the same game with priorities uniform over 0..3 (count-vector mode),
-loaded from device arrays and solved to device arrays through the C ABI, as
-the benchmark does (the loop as one CUDA graph).
+random game (out-degree U[2,5], owners p = 0.5, permuted priorities, seed 0),
+the 10,000,000-vertex ladder game and the random game with priorities uniform
+over 0..3 (count-vector mode), loaded from device arrays and solved to device
+arrays through the C ABI, as the benchmark does (the loop as one CUDA graph).
+
+* The final results, element for element: every output array of the full
+  solve (winners, both strategies, the dummies' choices, class, depth and
+  rank of every valuation) and the iteration counts against the oracle's full
+  solve of the same game, stored as SHA-256 digests and sampled values in
+  tests/golden/full_size_digests.json by tests/golden/make_full_size_digests.py
+  (which calls only the oracle; its solves take minutes on one core, longer
+  than a GPU test run may).
 
 * The start of the trajectory, element by element: the profile after the
   first three valuations (the iteration cap) and its valuation, against the
@@ -15,6 +23,10 @@ the benchmark does (the loop as one CUDA graph).
 The oracles take about half a minute per game (preprocessing, four
 valuations).
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -98,6 +110,38 @@ def assert_equal(got, want, keys, label):
             bad = np.nonzero(a != b)[0]
             raise AssertionError("%s: %s differs at %d vertices, first %s: got %s want %s" %
                                  (label, key, bad.size, bad[:5], a[bad[:5]], b[bad[:5]]))
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size_digests.json")
+FINAL_KEYS = ["win", "sigma", "tau", "val_class", "val_depth", "val_rank", "dummy_sigma"]
+
+
+def workload(name):
+    if name == "random-10m":
+        return gen.native_random_game(N, DMIN, DMAX, SEED)
+    return gen.ladder_game(N, SEED)
+
+
+@pytest.mark.parametrize("name", ["random-10m", "ladder-10m"])
+def test_full_size_final_results_equal_oracle(pg, ctx, name):
+    rec = json.load(open(GOLDEN))["workloads"][name]
+    g = workload(name)
+    h = hashlib.sha256()
+    for a in g.arrays():
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest() == rec["input_sha256"], "the generator changed: rerun tests/golden/make_full_size_digests.py"
+    rc, major, inner, used, iters, got = gpu_solve(pg, ctx, g)
+    assert rc == pg.PG_OK and used and iters == inner
+    bad = []
+    for key in FINAL_KEYS:
+        a, want = np.ascontiguousarray(got[key]), rec["arrays"][key]
+        assert str(a.dtype) == want["dtype"] and a.size == want["size"], key
+        idx = np.asarray(want["sample_index"], np.int64)
+        assert a[idx].astype(np.int64).tolist() == want["sample_value"], key  # sampled values, element by element
+        if hashlib.sha256(a.tobytes()).hexdigest() != want["sha256"]:
+            bad.append(key)
+    assert not bad, "%s: arrays differing from the oracle's full solve: %s" % (name, bad)
+    assert (major, inner) == (rec["major"], rec["inner"])
 
 
 def test_full_size_first_valuations(pg, ctx, game):

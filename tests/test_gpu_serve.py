@@ -1,6 +1,8 @@
 """Serving with continuous batching: games submitted while others are being
 solved are admitted between rounds, and every game's result is the one it
-gets alone (pg_solve, and the oracle)."""
+gets alone (pg_solve, and the oracle on every key, the dummies' choices
+included), for small games in waves and for games of 1e5-1e6 vertices in a
+layout with 64-bit edge offsets."""
 import time
 
 import numpy as np
@@ -75,10 +77,44 @@ def test_results_alone_and_in_the_mix(pg, ctx):
         for k in KEYS:
             assert np.array_equal(out[k], alone[k]), (i, g.n, k)
         assert (r["major"], r["inner"]) == (alone["major"], alone["inner"])
-        if i % 3 == 0:  # and the oracle
-            _, _, want = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
-            for k in KEYS[:-1]:
-                assert np.array_equal(out[k], np.asarray(want[k])), (i, k)
+        want = oracle_result(g)  # and the oracle, every key
+        for k in KEYS:
+            assert np.array_equal(out[k], np.asarray(want[k])), (i, k)
+        assert (r["major"], r["inner"]) == (want["major"], want["inner"]), i
+
+
+def oracle_result(g):
+    """The oracle's solve of g alone, with the dummies' choices (1 = their edge)."""
+    gp, r, want = o2.solve_game(g.n, g.offsets, g.targets, g.owner, g.pri)
+    want["dummy_sigma"] = (r["strat"][gp["n_orig"]:gp["n"]] != gp["n"]).astype(np.int8)
+    return want
+
+
+def test_large_games_with_wide_offsets_equal_oracle(pg):
+    """Games of 1e5-1e6 vertices (random and ladder) arriving while others are
+    resident, in a layout with 64-bit edge offsets (the layout of the largest
+    servers), each equal to the oracle's solve of it alone on every key."""
+    games = [gen.random_game(120_000, 2, 6, gen.batch_seed(7001)), gen.ladder_game(250_000, seed=7002),
+             gen.random_game(700_000, 2, 6, gen.batch_seed(7003)), gen.random_game(300_000, 2, 6, gen.batch_seed(7004)),
+             gen.random_game(1_000_000, 2, 6, gen.batch_seed(7005))]
+    sv = pg.pg_server_create(0, max_vertices=2_400_000, max_edges=12_000_000, max_games=4, round_iters=2,
+                             wide_offsets=True)
+    try:
+        for i, g in enumerate(games):  # one burst: the server admits what fits, the rest as room frees up
+            pg.pg_server_submit(sv, g.n, g.m, *g.arrays(), tag=i)
+        got = drain(pg, sv, len(games), timeout_s=300)
+        assert len(got) == len(games), pg.pg_server_error(sv)
+        stats = pg.pg_server_get_stats(sv)
+        results = {t: pg.pg_server_fetch(sv, t, got[t]["n"], got[t]["k"]) for t in got}
+    finally:
+        pg.pg_server_destroy(sv)
+    assert stats["max_resident"] > 1
+    for i, g in enumerate(games):
+        want = oracle_result(g)
+        assert got[i]["status"] == pg.PG_OK
+        for k in KEYS:
+            assert np.array_equal(results[i][k], np.asarray(want[k])), (i, g.n, k)
+        assert (got[i]["major"], got[i]["inner"]) == (want["major"], want["inner"]), i
 
 
 def test_iteration_cap_and_rejections(pg, ctx):

@@ -91,3 +91,63 @@ def test_two_ranks_shard_a_batch_over_gloo(tmp_path):
     o2.lib()  # the oracle library is built before the ranks start
     mp.spawn(_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     assert (tmp_path / "result").read_text() == "ok"
+
+
+STREAM, POOL = 40, 12
+
+
+def test_stream_assign_is_online_deterministic_and_balanced():
+    rng = np.random.default_rng(8)
+    for world in (1, 2, 3, 8):
+        w = rng.integers(1, 10_000, size=120)
+        owner = shard.stream_assign(w, world)
+        assert owner.shape == w.shape and owner.min() >= 0 and owner.max() < world
+        assert np.array_equal(owner, shard.stream_assign(w, world))
+        # online: the owners of the first arrivals do not depend on later ones
+        assert np.array_equal(shard.stream_assign(w[:50], world), owner[:50])
+        loads = np.bincount(owner, weights=w, minlength=world)
+        assert loads.max() - loads.min() <= w.max()  # greedy list scheduling bound
+    assert shard.stream_assign([3, 3, 3, 3], 2).tolist() == [0, 1, 0, 1]
+    with pytest.raises(ValueError):
+        shard.stream_assign([1], 0)
+
+
+def _stream_worker(rank, world, port, outdir):
+    """One rank of a sharded request stream: it takes the arrivals
+    stream_assign gives it (arrival j is game j mod POOL of a seeded pool),
+    solves each as its server would (the oracle stands in for the GPU solver
+    here), and the results meet on rank 0."""
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        vb, eb, off, tgt, own, pri = gen.native_batch(POOL, LO, HI, DMIN, DMAX, nthreads=1)
+        sizes = np.diff(vb)
+        arrival_game = np.arange(STREAM) % POOL
+        owner = shard.stream_assign(sizes[arrival_game], world)
+        mine = np.nonzero(owner == rank)[0]
+        results = {int(j): _solve_packed(vb, eb, off, tgt, own, pri, int(arrival_game[j])) for j in mine}
+        gathered = shard.gather_to_all(results)
+        served = shard.sum_over_ranks(len(results))
+        if rank == 0:
+            merged = {}
+            for part in gathered:
+                assert not set(part) & set(merged), "an arrival served on two ranks"
+                merged.update(part)
+            want = {j: _solve_packed(vb, eb, off, tgt, own, pri, int(arrival_game[j])) for j in range(STREAM)}
+            ok = sorted(merged) == list(range(STREAM)) and all(merged[j] == want[j] for j in range(STREAM)) \
+                and served == STREAM and all(len(p) > 0 for p in gathered)
+            with open(os.path.join(outdir, "result"), "w") as f:
+                f.write("ok" if ok else "mismatch")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_shard_a_request_stream_over_gloo(tmp_path):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    if not torch.distributed.is_available():
+        pytest.skip("torch.distributed is not available")
+    from oracle import o2
+    o2.lib()
+    mp.spawn(_stream_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    assert (tmp_path / "result").read_text() == "ok"
