@@ -148,9 +148,12 @@ pg_status pg_game_info(const pg_game *game, int32_t *n, int64_t *m, int32_t *k);
  * out of direct steps and were finished by pointer jumping, the jumping
  * rounds, finite vertices, vertices reaching an odd cycle, parents ranked
  * by one block, parents ranked by the id-ordered scan, and the switches of
- * the last switching pass. */
+ * the last switching pass; deep = 1 if it took the ruling-set path
+ * (pg_set_tuning), with its rulers and its pointer-jumping rounds over the
+ * g-forest and over the rulers. */
 typedef struct {
     int32_t n_pending, jump_rounds, n_fin, n_odd, n_big, n_huge, n_switch;
+    int32_t deep, n_rulers, deep_rounds, rs_rounds;
 } pg_counters;
 pg_status pg_game_counters(const pg_game *game, pg_counters *out);
 
@@ -383,6 +386,24 @@ pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuatio
  * synchronises once per iteration. Both give identical results. The paper has
  * no counterpart (it concerns launching work on the device only). */
 pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
+/* Work partitioning of the valuation, per context (the paper has no
+ * counterpart; results never depend on it):
+ *   deep_cut    a g-chain walk longer than this (the play rises that many
+ *               times) sends the game to the ruling-set path for the rest of
+ *               the call: the Euler tour of the nearest-greater forest ranked
+ *               by a sparse ruling set (Section 5's list ranking), work linear
+ *               in n whatever the forest's depth; default 64;
+ *   ruler_bits  the ruling set takes about one list element in 2^ruler_bits as
+ *               a ruler (1..16); default 5.
+ * pg_set_tuning ignores zero fields; PG_EINVAL for negative values or
+ * ruler_bits > 16. */
+typedef struct {
+    int32_t deep_cut;
+    int32_t ruler_bits;
+} pg_tuning;
+pg_status pg_set_tuning(pg_ctx *ctx, const pg_tuning *t);
+pg_status pg_get_tuning(const pg_ctx *ctx, pg_tuning *t);
+
 /* Edge offsets of the packed layout of pg_solve_batch: 32-bit while the batch
  * holds fewer than 2^31 edges, 64-bit beyond. enable = 1 takes 64-bit offsets
  * at any size (the layout of the largest batches, e.g. to check it on small

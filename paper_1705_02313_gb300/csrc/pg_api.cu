@@ -87,7 +87,9 @@ void free_game(pg_game* g) {
                     g->tgt,     g->flags, g->pri,   g->nid0,  g->orig_of, g->dnid,    g->dummy_of,
                     g->strat, g->gd,     g->gd32,  g->kind,  g->plist, g->slot,  g->ccnt,  g->coff,    g->cl_ks,   g->sz,
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
-                    g->tiles, g->tsum,   g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128};
+                    g->tiles, g->tsum,   g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128,
+                    g->d_anc, g->d_sc, g->d_podd, g->d_peven, g->d_oddL, g->d_evenL, g->d_nxt, g->d_wt, g->d_loc,
+                    g->d_own, g->d_rid, g->d_rl, g->d_val, g->d_rnx};
     int prev = -1;
     const bool switched =
         cudaGetDevice(&prev) == cudaSuccess && prev != g->device && cudaSetDevice(g->device) == cudaSuccess;
@@ -322,7 +324,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t* gactive
                             int64_t hard_cap) {
     const int64_t it = *iters + 1;
     *iters = it;
-    cudaGraphSetConditional(h, (gactive[0] > 0 && c->err == 0 && it < hard_cap) ? 1u : 0u);
+    cudaGraphSetConditional(h, (gactive[0] > 0 && c->err == 0 && c->deep == 0 && it < hard_cap) ? 1u : 0u);
 }
 
 // One iteration of Algorithm 1 for every game of g (enqueued on ctx->stream).
@@ -343,7 +345,8 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     const int w = even ? 1 : 0;
     if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit && g->loop_reset[w] == g->reset_tau &&
-        g->loop_cmp[w] == loop_compares(g))
+        g->loop_cmp[w] == loop_compares(g) && g->loop_deep[w] == g->deep_mode && g->loop_cut[w] == ctx->deep_cut &&
+        g->loop_rbits[w] == ctx->ruler_bits)
         return true;
     if (g->loop_exec[w]) {
         cudaGraphExecDestroy(g->loop_exec[w]);
@@ -410,6 +413,9 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     g->loop_limit[w] = limit;
     g->loop_reset[w] = g->reset_tau;
     g->loop_cmp[w] = loop_compares(g);
+    g->loop_deep[w] = g->deep_mode;
+    g->loop_cut[w] = ctx->deep_cut;
+    g->loop_rbits[w] = ctx->ruler_bits;
     return true;
 }
 
@@ -424,11 +430,11 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
 // synchronises once per iteration. A positive limit ends the call after that
 // many iterations even if games are still active (their state stays on the
 // device and a later call continues them).
-pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit) {
+pg_status run_loop_once(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit, int64_t* ran) {
     pg_ctx* ctx = g->ctx;
     g->last_graph = false;
+    *ran = 0;
     const bool cmp = loop_compares(g);
-    g->last_cmp = cmp;
     const int64_t hard = limit > 0 ? std::min<int64_t>(limit, cap + 2) : cap + 2;
     if (!tm.on && ctx->graphs && build_loop_graph(g, cap, even, hard)) {
         const int w = even ? 1 : 0;
@@ -439,6 +445,7 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(it, g->loop_iters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         pg_status st = sync_counters(g);
         const int64_t iters = *it;
+        *ran = iters;
         g->t_vals += iters;
         ctx->launches += g->loop_launch[w] * iters;
         for (int i = 0; i < KID_COUNT; ++i) g->klaunch[i] += g->loop_klaunch[w][i] * iters;
@@ -462,9 +469,32 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
         st = sync_counters(g);
         if (st) return st;
         ++g->t_vals;
+        *ran = it;
         g->t_val += tm.since(0, 1);
         g->t_switch += tm.since(1, 2);
-        if (ctx->pinned[0] == 0 || it >= hard) return PG_OK;
+        if (ctx->pinned[0] == 0 || it >= hard || g->hcnt->deep) return PG_OK;
+    }
+}
+
+// The loop of Algorithm 1 (run_loop_once) until its end, a cap or the limit.
+// When an iteration finds a g-chain longer than the cutover depth, it is
+// abandoned before anything is switched or counted, the loop stops, and the
+// game continues from the same profile with the ruling-set ranks (for the
+// rest of this call), so the trajectory is unchanged.
+pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit) {
+    int64_t done = 0;
+    for (;;) {
+        int64_t ran = 0;
+        pg_status st = run_loop_once(g, cap, even, tm, limit > 0 ? limit - done : 0, &ran);
+        if (st) return st;
+        g->last_cmp = loop_compares(g);
+        if (g->cv || g->deep_mode || !g->hcnt->deep) return PG_OK;
+        g->deep_mode = true;
+        st = prepare_deep(g);
+        if (st) return st;
+        g->t_vals -= 1;  // the abandoned iteration
+        done += ran - 1;
+        if (limit > 0 && done >= limit) return PG_OK;
     }
 }
 
@@ -518,6 +548,22 @@ pg_status pg_release_cached_memory(int device) {
 pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;
     ctx->graphs = enable != 0;
+    return PG_OK;
+}
+
+pg_status pg_set_tuning(pg_ctx* ctx, const pg_tuning* t) {
+    if (!ctx || !t) return PG_EINVAL;
+    if (t->deep_cut < 0 || t->ruler_bits < 0 || t->ruler_bits > 16) return fail(ctx, PG_EINVAL, "pg_set_tuning: bad value");
+    if (t->deep_cut) ctx->deep_cut = t->deep_cut;
+    if (t->ruler_bits) ctx->ruler_bits = t->ruler_bits;
+    return PG_OK;
+}
+
+pg_status pg_get_tuning(const pg_ctx* ctx, pg_tuning* t) {
+    if (!ctx || !t) return PG_EINVAL;
+    *t = pg_tuning{};
+    t->deep_cut = ctx->deep_cut;
+    t->ruler_bits = ctx->ruler_bits;
     return PG_OK;
 }
 
@@ -607,7 +653,8 @@ pg_status pg_game_info(const pg_game* g, int32_t* n, int64_t* m, int32_t* k) {
 pg_status pg_game_counters(const pg_game* g, pg_counters* out) {
     if (!g || !out || !g->hcnt) return PG_EINVAL;
     const Counters& c = *g->hcnt;  // copied to the host at the end of every valuation
-    *out = {c.n_pending, c.jump_rounds, c.n_fin, c.n_odd, c.n_big, c.n_huge, c.n_switch};
+    *out = {c.n_pending, c.jump_rounds, c.n_fin, c.n_odd, c.n_big, c.n_huge, c.n_switch,
+            g->val_deep ? 1 : 0, c.n_rulers, c.deep_rounds, c.rs_rounds};
     return PG_OK;
 }
 
@@ -648,8 +695,7 @@ pg_status pg_solve(pg_game* g, const pg_solve_opts* opts, pg_result* out) {
         return fail(ctx, PG_ENOTADMISSIBLE, "pg_solve: an odd cycle was reached: sigma is not admissible");
     const bool timed_out = gs.phase == kPhaseTimeout;
     if (timed_out || g->last_cmp) {
-        st = enqueue_valuation(g, false);  // the full valuation of the profile being returned
-        if (!st) st = sync_counters(g);
+        st = full_valuation(g, false);  // the full valuation of the profile being returned
         if (st) return st;
         g->last_cmp = false;
     }
@@ -697,8 +743,7 @@ pg_status pg_best_response(pg_game* g, const int32_t* sigma, const int8_t* dummy
         if (st) return st;
         if (out->dom) {
             // dom needs a valuation that records it
-            st = enqueue_valuation(g, true);
-            if (!st) st = sync_counters(g);
+            st = full_valuation(g, true);
             if (st) return st;
             st = write_outputs(g, out->mem_kind, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, out->dom,
                                nullptr);
@@ -751,11 +796,9 @@ pg_status pg_valuate(pg_game* g, const int32_t* sigma, const int8_t* dummy_sigma
     if (st) return st;
     Timer tm(g);
     tm.mark(0);
-    st = enqueue_valuation(g, true);
+    st = full_valuation(g, true);
     if (st) return st;
     tm.mark(1);
-    st = sync_counters(g);
-    if (st) return st;
     g->t_val = g->t_total = tm.since(0, 1);
     g->t_vals = 1;
     if (out) {

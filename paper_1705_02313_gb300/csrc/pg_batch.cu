@@ -262,8 +262,7 @@ pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int6
         any_odd |= x.phase == kPhaseOddCycle;
     }
     if (any_timeout || g->last_cmp) {  // the full valuation of the profiles being returned
-        st = enqueue_valuation(g, false);
-        if (!st) st = sync_counters(g);
+        st = full_valuation(g, false);
         if (st) return st;
         g->last_cmp = false;
     }

@@ -81,9 +81,18 @@ struct Counters {
     uint32_t bar_count;  // software grid barrier
     uint32_t bar_gen;
     int32_t jump_rounds;
+    int32_t deep;         // a chain walk passed the cutover depth: the valuation needs the ruling-set path
+    int32_t n_dlist;      // ruling-set path: vertices whose root is found by pointer jumping
+    int32_t deep_rounds;  //   rounds of that pointer jumping
+    int32_t n_dmid;       //   segments sorted in shared memory
+    int32_t n_dbig;       //   segments sorted by the global-memory radix sort
+    int32_t n_rulers;     //   rulers of the list ranking
+    int32_t rs_rounds;    //   pointer-jumping rounds over the rulers
+    int32_t rs_buf;       //   the buffer holding the rulers' suffix sums
 };
 constexpr int32_t kErrJumpRounds = 1;   // pointer jumping exceeded its round cap
 constexpr int32_t kErrBarrier = 2;      // a grid barrier waited past its spin limit
+constexpr int32_t kErrRulers = 4;       // the list ranking's rulers overflowed their scratch, or a sublist never ended
 
 // Kernel classes of one iteration, for per-kernel device timing.
 enum KernelId {
@@ -98,6 +107,7 @@ enum KernelId {
     KID_SWITCH_ODD,  // k_switch for Odd
     KID_SWITCH_EVEN, // k_switch for Even
     KID_CLASSIFY,    // k_classify (loop iterations that compare valuations instead of ranking them)
+    KID_DEEP,        // the ruling-set ranks of a deep g-forest (pg_deep.cu), after K1
     KID_COUNT
 };
 extern const char* const kKernelNames[KID_COUNT];
@@ -128,6 +138,8 @@ struct pg_ctx {
     bool graphs = true;         // run the iteration loop as one CUDA graph with a device-side condition
     bool loop_ranks = false;    // loop iterations rank every valuation (else they only compare them)
     bool wide_offsets = false;  // batches take 64-bit edge offsets at any size (else from 2^31 edges)
+    int32_t deep_cut = 64;      // a g-chain walk longer than this switches the game to the ruling-set ranks
+    int32_t ruler_bits = 5;     // the ruling set takes about one list element in 2^ruler_bits as a ruler
     cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
 
@@ -231,9 +243,31 @@ struct pg_game {
     int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
     bool last_graph = false;     // the last loop ran as a graph
     bool last_cmp = false;       // the last loop compared valuations: key, cls and depth are not the current ones
+    // ruling-set ranks (pg_deep.cu), for games whose g-forest is deep
+    bool deep_mode = false;      // every valuation of the current call takes the ruling-set path
+    bool val_deep = false;       // the last valuation took it (its depths are written; no depth pass)
+    int32_t* d_anc = nullptr;    // [n] root of each vertex's g-chain
+    uint8_t* d_sc = nullptr;     // [2n] the sink's odd and even children (flags for the compactions)
+    int32_t* d_podd = nullptr;   // [n+1] positions of the sink's odd children
+    int32_t* d_peven = nullptr;  // [n+1] positions of the sink's even children
+    int32_t* d_oddL = nullptr;   // [n] the sink's odd children, by id
+    int32_t* d_evenL = nullptr;  // [n] the sink's even children, by id
+    int32_t* d_nxt = nullptr;    // [2n] Euler tour: next element
+    int2* d_wt = nullptr;        // [2n] element weights (visits, depth)
+    int2* d_loc = nullptr;       // [2n] prefix within the ruler's sublist
+    int32_t* d_own = nullptr;    // [2n] the element's ruler
+    int32_t* d_rid = nullptr;    // [2n] ruler index of a ruler element, else -1
+    int32_t* d_rl = nullptr;     // [rcap] element of each ruler
+    int2* d_val = nullptr;       // [2 rcap] suffix sums of the rulers (two buffers)
+    int32_t* d_rnx = nullptr;    // [2 rcap] next ruler (two buffers)
+    int32_t d_rcap = 0;          // rulers the scratch holds
+    int d_coop = 0;              // co-resident blocks of the ruling-set path's cooperative kernels
     bool reset_tau = false;      // SI-Reset (Section 6): Odd restarts from its first edges after every Even switch
     bool loop_reset[2] = {false, false};  // the SI-Reset setting each loop graph was built with
     bool loop_cmp[2] = {false, false};    // each loop graph compares valuations (loop_compares)
+    bool loop_deep[2] = {false, false};   // each loop graph ranks through the ruling-set path
+    int32_t loop_cut[2] = {0, 0};         // the cutover depth each loop graph was built with
+    int32_t loop_rbits[2] = {0, 0};       // the ruler stride each loop graph was built with
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;
@@ -325,6 +359,15 @@ pg_status enqueue_valuation_cmp(pg_game* g);
 pg_status enqueue_switch_cmp(pg_game* g, int player);
 // After a loop that compared valuations: the full valuation of the current profile (key, cls, depth).
 pg_status finish_loop(pg_game* g);
+// K1 alone (counters cleared, nearest-greater walks and pointer jumping with walk lengths).
+pg_status enqueue_k1(pg_game* g);
+// The valuation through the ruling-set ranks of an Euler tour (pg_deep.cu): cls, depth, key, dom.
+pg_status enqueue_valuation_deep(pg_game* g, bool want_dom);
+// Allocates (once, and again for denser rulers) the ruling-set path's scratch; not under stream capture.
+pg_status prepare_deep(pg_game* g);
+// One valuation on the host's schedule: the default path, and the ruling-set path if a chain walk
+// passed the cutover depth (the game then stays on it for the rest of the call). Waits for the stream.
+pg_status full_valuation(pg_game* g, bool want_dom);
 // Copies the counters to g->hcnt and waits for the stream; checks device error bits.
 pg_status sync_counters(pg_game* g);
 // Count-vector mode (pg_cv.cu): scratch, one valuation, one switching pass, counts output.

@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
                                                    int32_t* sz, int32_t* ccnt, int32_t* __restrict__ slot,
                                                    uint8_t* __restrict__ kind, uint8_t* __restrict__ cls,
                                                    int32_t* __restrict__ dom, int want_dom,
-                                                   const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt) {
+                                                   const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt,
+                                                   int32_t deep_cut) {
     if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
     __shared__ int32_t tkey[kHotSlots], tcnt[kHotSlots];
     for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
@@ -362,7 +363,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
             len[j] = 0;
             act[j] = v[j] < n && !slotid[j] && !g32_none(w) && !sinkchild[j];
         }
-        // classification walks (len: the vertices from g(v) to the chain's end)
+        // classification walks (len: the vertices from g(v) to the chain's end); a walk longer than deep_cut
+        // hands the valuation to the ruling-set path and stops (its vertex takes no further part here)
+        bool cut[kIlpChain1];
+#pragma unroll
+        for (int j = 0; j < kIlpChain1; ++j) cut[j] = false;
         for (;;) {
             bool any = false;
             uint32_t wx[kIlpChain1];
@@ -370,6 +375,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
             for (int j = 0; j < kIlpChain1; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
 #pragma unroll
             for (int j = 0; j < kIlpChain1; ++j) {
+                if (act[j] && len[j] >= deep_cut) {
+                    cut[j] = true;
+                    act[j] = false;
+                    cnt->deep = 1;
+                }
                 if (act[j]) {
                     ++len[j];
                     if (g32_none(wx[j])) {
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
         bool deep[kIlpChain1];
 #pragma unroll
         for (int j = 0; j < kIlpChain1; ++j) {
-            act[j] = v[j] < n && !slotid[j] && cyc[j] < 0 && !sinkchild[j];
+            act[j] = v[j] < n && !slotid[j] && cyc[j] < 0 && !sinkchild[j] && !cut[j];
             sl[j] = act[j] ? atomicAdd(ccnt + g[j], 1) : -1;
             x[j] = g[j];
             deep[j] = len[j] >= kDeepChain;
@@ -461,7 +471,9 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int32_t n, const uint32_t* _
                                                     const uint8_t* __restrict__ kind, const int32_t* __restrict__ sz,
                                                     const int32_t* __restrict__ coff, const int32_t* __restrict__ slot,
                                                     int32_t* __restrict__ ccnt, int2* __restrict__ cl_ks,
-                                                    int32_t* __restrict__ sinkval, int64_t* __restrict__ tsum) {
+                                                    int32_t* __restrict__ sinkval, int64_t* __restrict__ tsum,
+                                                    const Counters* cnt) {
+    if (cnt->deep) return;  // the ruling-set path takes over (and clears the children counts)
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -524,6 +536,7 @@ __global__ void __launch_bounds__(kBlock) k_siblings(int32_t n, const int32_t* _
                                                      const int2* __restrict__ cl_ks, int32_t* __restrict__ wgt,
                                                      int32_t* __restrict__ oddsz, int32_t* biglist,
                                                      int32_t* hugelist, Counters* cnt) {
+    if (cnt->deep) return;
     const int lane = threadIdx.x & 31;
     for (int32_t a0 = blockIdx.x * blockDim.x; a0 < n; a0 += gridDim.x * blockDim.x) {
         const int32_t a = a0 + threadIdx.x;
@@ -577,6 +590,7 @@ __global__ void __launch_bounds__(kBlock) k_big_parents(const int32_t* __restric
                                                         const int32_t* __restrict__ biglist,
                                                         int32_t* __restrict__ wgt, int32_t* __restrict__ oddsz,
                                                         const Counters* cnt) {
+    if (cnt->deep) return;
     __shared__ int2 sk[kHugeChildren];
     __shared__ int32_t wsum[kBlock / 32];
     __shared__ int32_t carry_s, odd_s;
@@ -727,6 +741,7 @@ constexpr int kTileScanThreads = 1024;
 __global__ void __launch_bounds__(kTileScanThreads) k_tiles_scan(int64_t* __restrict__ tsum, int64_t* tiles,
                                                                  int64_t ntiles, int32_t sink_key, int64_t* gscan,
                                                                  int32_t* key, Counters* cnt) {
+    if (cnt->deep) return;
     __shared__ int64_t se[kTileScanThreads / 32], so[kTileScanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t ce = 0, co = 0;
@@ -815,6 +830,7 @@ __global__ void __launch_bounds__(kBlock) k_game_prefix(int32_t n, int32_t ngame
                                                         const int32_t* __restrict__ sinkval,
                                                         const int64_t* __restrict__ tiles, int64_t* gscan,
                                                         int32_t* key, Counters* cnt) {
+    if (cnt->deep) return;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ngames; gi += nw) {
@@ -836,7 +852,9 @@ __global__ void __launch_bounds__(kBlock) k_game_prefix(int32_t n, int32_t ngame
 __global__ void __launch_bounds__(kBlock) k_sink_apply(int32_t n, const int32_t* __restrict__ sinkval,
                                                        const int64_t* __restrict__ tiles,
                                                        const int32_t* __restrict__ vgame,
-                                                       const int64_t* __restrict__ gscan, int32_t* __restrict__ wgt) {
+                                                       const int64_t* __restrict__ gscan, int32_t* __restrict__ wgt,
+                                                       const Counters* cnt) {
+    if (cnt->deep) return;
     const int64_t i0 = (int64_t)blockIdx.x * kCoopTile + (int64_t)threadIdx.x * kCIpt;
     int32_t v[kCIpt];
     load8(sinkval, n, i0, v);
@@ -873,6 +891,7 @@ __global__ void __launch_bounds__(kBlock) k_idscan_coop(int32_t n, const uint32_
                                                         const uint8_t* __restrict__ kind,
                                                         const int32_t* __restrict__ hugelist, int64_t* tiles,
                                                         int64_t ntiles, int32_t* wgt, int32_t* oddsz, Counters* cnt) {
+    if (cnt->deep) return;  // uniform over the grid: no block reaches a barrier
     const int32_t nh = cnt->n_huge;
     for (int32_t h = 0; h < nh; ++h) {
         const int32_t a = hugelist[h];
@@ -953,7 +972,7 @@ __global__ void __launch_bounds__(kBlock) k_chain2(int32_t n, const uint32_t* __
                                                    const uint8_t* __restrict__ kind, const int32_t* __restrict__ wgt,
                                                    const int32_t* __restrict__ oddsz, int32_t* __restrict__ key,
                                                    const Counters* cnt) {
-    if (cnt->err) return;  // unfinished jumping: no chain walk
+    if (cnt->err || cnt->deep) return;  // unfinished jumping or a deep forest: no chain walk
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -1036,6 +1055,7 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
                                                    const int32_t* __restrict__ key, const int32_t* __restrict__ vgame,
                                                    const int32_t* __restrict__ gsink, int32_t sink0, GameState* gst,
                                                    int32_t* strat, Counters* cnt) {
+    if (cnt->deep) return;  // the ranks were not computed: the loop stops and continues on the ruling-set path
     if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
         const GameState st = gst[0];
         if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
@@ -1102,7 +1122,8 @@ __global__ void __launch_bounds__(kBlock) k_switch(int32_t n, int player, const 
 // iteration when Even switched, stop at the cap. Counts the games still active.
 // With reset_mode, a game whose Even player switched is marked for k_reset_odd.
 __global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even_phase, int reset_mode,
-                           int32_t* gactive) {
+                           int32_t* gactive, const Counters* cnt) {
+    if (cnt->deep) return;  // an abandoned iteration: nothing counted, no game active (the loop stops)
     int32_t act = 0;
     for (int32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngames; gi += gridDim.x * blockDim.x) {
         GameState st = gst[gi];
@@ -1133,7 +1154,8 @@ __global__ void __launch_bounds__(kBlock) k_reset_odd(int32_t n, const OffT* __r
                                                       const int32_t* __restrict__ tgt,
                                                       const uint8_t* __restrict__ flags,
                                                       const int32_t* __restrict__ vgame, const GameState* gst,
-                                                      int32_t* strat) {
+                                                      int32_t* strat, const Counters* cnt) {
+    if (cnt->deep) return;
     if (!vgame && !gst[0].reset) return;
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const uint8_t f = flags[v];
@@ -1177,18 +1199,19 @@ __device__ inline int32_t top_id(uint32_t t) { return (int32_t)(t & 0x3fffffffu)
 // (sigma not admissible).
 __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags,
                                                      uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
-                                                     GameState* gst, const Counters* cnt) {
+                                                     GameState* gst, Counters* cnt, int32_t deep_cut) {
     if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
          tile += nwarps) {
-        int32_t v[kIlp], x[kIlp];
+        int32_t v[kIlp], x[kIlp], len[kIlp];
         uint32_t w0[kIlp];
         bool act[kIlp], top[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            len[j] = 0;
             const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
             w0[j] = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
             top[j] = g32_none(w0[j]);
@@ -1204,6 +1227,10 @@ __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, 
             for (int j = 0; j < kIlp; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
+                if (act[j] && ++len[j] > deep_cut) {  // a deep forest: the iteration is abandoned (loop stops)
+                    act[j] = false;
+                    cnt->deep = 1;
+                }
                 if (act[j]) {
                     if (wx[j] & kG32Top) {  // a none vertex, or one already marked TOP
                         top[j] = true;
@@ -1308,7 +1335,7 @@ __global__ void __launch_bounds__(kBlock) k_switch_cmp(int32_t n, int player, co
                                                        const int32_t* __restrict__ vgame,
                                                        const int32_t* __restrict__ gsink, int32_t sink0,
                                                        GameState* gst, int32_t* strat, Counters* cnt) {
-    if (cnt->err) return;  // unfinished jumping: no comparison walk
+    if (cnt->err || cnt->deep) return;  // unfinished jumping, or a deep forest (the loop stops)
     if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
         const GameState st = gst[0];
         if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
@@ -1378,7 +1405,7 @@ __global__ void __launch_bounds__(kBlock) k_switch_cmp(int32_t n, int player, co
 
 const char* const kKernelNames[KID_COUNT] = {"walk",     "jump",      "chain1", "child_scan", "scatter",
                                               "siblings", "sink_scan", "chain2", "switch_odd", "switch_even",
-                                              "classify"};
+                                              "classify", "ruling_set"};
 
 void prof_begin(pg_game* g, int id) {
     if (g->ctx->timing) cudaEventRecord(g->kev[2 * id], g->ctx->stream);
@@ -1474,6 +1501,8 @@ pg_status chain1_blocks_for(pg_ctx* ctx, int* out) {
 
 pg_status reset_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
+    g->deep_mode = false;  // every call starts on the default path; a deep g-forest switches it
+    g->val_deep = false;
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
@@ -1489,16 +1518,13 @@ pg_status reset_games(pg_game* g) {
     return PG_OK;
 }
 
-pg_status enqueue_valuation(pg_game* g, bool want_dom) {
-    if (g->cv) return enqueue_valuation_cv(g, want_dom);
+pg_status enqueue_k1(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     int32_t n = g->n;
     Counters* c = g->cnt;
-    const unsigned grid = grid_for(n);
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    // walks here are short but for a few: one pass of kWalkCap steps straight into the jumping list
     k_walk<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd,
                                                     g->gd32, g->plist, g->sz, g->oddsz, c, &c->n_pending);
     prof_end(g, KID_WALK, 1);
@@ -1511,20 +1537,36 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
         prof_end(g, KID_JUMP, 1);
     }
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status enqueue_valuation(pg_game* g, bool want_dom) {
+    if (g->cv) return enqueue_valuation_cv(g, want_dom);
+    if (g->deep_mode) return enqueue_valuation_deep(g, want_dom);
+    g->val_deep = false;
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    int32_t n = g->n;
+    Counters* c = g->cnt;
+    const unsigned grid = grid_for(n);
+    // K1: walks here are short but for a few, one pass of kWalkCap steps straight into the jumping list
+    pg_status st1 = enqueue_k1(g);
+    if (st1) return st1;
     prof_begin(g, KID_CHAIN1);
     // one wave of resident blocks for a single game; packed games (batches, servers) keep one block per 8 tiles,
     // which measured faster there (4,096-game batch: 5.95 s of loop against 6.52 s)
     const unsigned c1grid =
         (g->chain1_blocks > 0 && !g->vgame) ? std::min(ilp_grid(n), (unsigned)g->chain1_blocks) : ilp_grid(n);
     k_chain1<<<c1grid, kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls,
-                                       g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c);
+                                       g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c, ctx->deep_cut);
     prof_end(g, KID_CHAIN1, 1);
     prof_begin(g, KID_CSCAN);
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
     prof_end(g, KID_CSCAN, 3);
     prof_begin(g, KID_SCATTER);
     k_scatter<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->kind, g->sz, g->coff, g->slot, g->ccnt, g->cl_ks, g->sinkval,
-                                             g->tsum);
+                                             g->tsum, c);
     prof_end(g, KID_SCATTER, 1);
     prof_begin(g, KID_SIBLINGS);
     k_siblings<<<grid, kBlock, 0, s>>>(n, g->coff, g->cl_ks, g->wgt, g->oddsz, g->plist, g->hugelist, c);
@@ -1544,7 +1586,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
             const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + 7) / 8, 4096));
             k_game_prefix<<<gp, kBlock, 0, s>>>(n, g->ngames, g->gsink, g->sinkval, g->tiles, g->gscan, g->key, c);
         }
-        k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->vgame, g->gscan, g->wgt);
+        k_sink_apply<<<(unsigned)g->ntiles, kBlock, 0, s>>>(n, g->sinkval, g->tiles, g->vgame, g->gscan, g->wgt, c);
         prof_end(g, KID_SINKSCAN, single ? 3 : 4);
     }
     prof_begin(g, KID_CHAIN2);
@@ -1555,6 +1597,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
 }
 
 pg_status enqueue_depth(pg_game* g) {
+    if (g->val_deep) return PG_OK;  // the ruling-set path wrote the depths with the ranks
     pg_ctx* ctx = g->ctx;
     ctx->launches += 1;
     k_depth<<<grid_for(g->n), kBlock, 0, ctx->stream>>>(g->n, g->gd, g->kind, g->depth, g->cnt);
@@ -1586,7 +1629,8 @@ pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gactive, 0, sizeof(int32_t), s));
     ctx->launches += 1;
     const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + kBlock - 1) / kBlock, 1024));
-    k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->reset_tau ? 1 : 0, g->gactive);
+    k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->reset_tau ? 1 : 0, g->gactive,
+                                    g->cnt);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
@@ -1597,15 +1641,15 @@ pg_status enqueue_reset(pg_game* g) {
     ctx->launches += 1;
     if (g->off64)
         k_reset_odd<int64_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, g->off64, g->tgt, g->flags, g->vgame, g->gst,
-                                                               g->strat);
+                                                               g->strat, g->cnt);
     else
         k_reset_odd<int32_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, g->off, g->tgt, g->flags, g->vgame, g->gst,
-                                                               g->strat);
+                                                               g->strat, g->cnt);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
 
-bool loop_compares(const pg_game* g) { return !g->cv && !g->ctx->loop_ranks; }
+bool loop_compares(const pg_game* g) { return !g->cv && !g->ctx->loop_ranks && !g->deep_mode; }
 
 pg_status enqueue_valuation_cmp(pg_game* g) {
     pg_ctx* ctx = g->ctx;
@@ -1628,7 +1672,8 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     }
     prof_begin(g, KID_CLASSIFY);
     // the top words live in the chain-weight array, which only a full valuation uses
-    k_classify<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame, g->gst, c);
+    k_classify<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame, g->gst, c,
+                                              ctx->deep_cut);
     prof_end(g, KID_CLASSIFY, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
@@ -1653,9 +1698,18 @@ pg_status enqueue_switch_cmp(pg_game* g, int player) {
 
 pg_status finish_loop(pg_game* g) {
     if (!g->last_cmp) return PG_OK;
-    pg_status st = enqueue_valuation(g, false);
-    if (!st) st = sync_counters(g);
+    pg_status st = full_valuation(g, false);
     if (!st) g->last_cmp = false;
+    return st;
+}
+
+pg_status full_valuation(pg_game* g, bool want_dom) {
+    pg_status st = enqueue_valuation(g, want_dom);
+    if (!st) st = sync_counters(g);
+    if (st || g->cv || g->val_deep || !g->hcnt->deep) return st;
+    g->deep_mode = true;  // a chain walk passed the cutover: the ruling-set path, for the rest of the call
+    st = enqueue_valuation_deep(g, want_dom);
+    if (!st) st = sync_counters(g);
     return st;
 }
 
@@ -1667,6 +1721,7 @@ pg_status sync_counters(pg_game* g) {
     prof_collect(g);
     if (g->hcnt->err & kErrBarrier) return fail(ctx, PG_ECUDA, "valuation: a grid barrier timed out");
     if (g->hcnt->err & kErrJumpRounds) return fail(ctx, PG_ECUDA, "valuation: pointer jumping did not converge");
+    if (g->hcnt->err & kErrRulers) return fail(ctx, PG_ECUDA, "valuation: the ruling-set list ranking failed");
     return PG_OK;
 }
 

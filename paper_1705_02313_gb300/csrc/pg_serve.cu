@@ -481,8 +481,7 @@ void worker_main(pg_server* sv) {
         }
         if (!any_done) continue;
         if (any_timeout || sv->B->last_cmp) {  // results describe the profile being returned (full valuation)
-            st = enqueue_valuation(sv->B, false);
-            if (!st) st = sync_counters(sv->B);
+            st = full_valuation(sv->B, false);
             if (st) {
                 set_fatal(sv, st, ctx);
                 return;

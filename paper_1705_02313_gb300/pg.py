@@ -63,6 +63,10 @@ class pg_server_opts(C.Structure):
                 ("round_iters", C.c_int32), ("max_inner", C.c_int64), ("wide_offsets", C.c_int32)]
 
 
+class pg_tuning(C.Structure):
+    _fields_ = [("deep_cut", C.c_int32), ("ruler_bits", C.c_int32)]
+
+
 class pg_served(C.Structure):
     _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("n", C.c_int32), ("k", C.c_int32),
                 ("major", C.c_int64), ("inner", C.c_int64), ("queue_us", C.c_double), ("latency_us", C.c_double)]
@@ -116,6 +120,8 @@ def lib():
     L.pg_set_graphs.argtypes = [P, I32]
     L.pg_set_loop_ranks.argtypes = [P, I32]
     L.pg_set_wide_offsets.argtypes = [P, I32]
+    L.pg_set_tuning.argtypes = [P, C.POINTER(pg_tuning)]
+    L.pg_get_tuning.argtypes = [P, C.POINTER(pg_tuning)]
     L.pg_release_cached_memory.argtypes = [C.c_int]
     L.pg_last_loop.argtypes = [P, C.POINTER(I32), C.POINTER(I64)]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -135,7 +141,7 @@ def lib():
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_set_wide_offsets", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_set_wide_offsets", "pg_set_tuning", "pg_get_tuning", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
                  "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters", "pg_best_response_bf"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -240,7 +246,7 @@ def pg_game_info(game):
 
 class pg_counters(C.Structure):
     _fields_ = [(nm, C.c_int32) for nm in ["n_pending", "jump_rounds", "n_fin", "n_odd", "n_big", "n_huge",
-                                           "n_switch"]]
+                                           "n_switch", "deep", "n_rulers", "deep_rounds", "rs_rounds"]]
 
 
 def pg_game_counters(game):
@@ -469,6 +475,18 @@ def pg_set_timing(ctx, enable):
 
 def pg_set_graphs(ctx, enable):
     _check(ctx, lib().pg_set_graphs(ctx, 1 if enable else 0), "pg_set_graphs")
+
+
+def pg_set_tuning(ctx, deep_cut=0, ruler_bits=0):
+    """Sets the work partitioning of the valuation (zero keeps a value)."""
+    t = pg_tuning(int(deep_cut), int(ruler_bits))
+    _check(ctx, lib().pg_set_tuning(ctx, C.byref(t)), "pg_set_tuning")
+
+
+def pg_get_tuning(ctx):
+    t = pg_tuning()
+    _check(ctx, lib().pg_get_tuning(ctx, C.byref(t)), "pg_get_tuning")
+    return {"deep_cut": t.deep_cut, "ruler_bits": t.ruler_bits}
 
 
 def pg_set_wide_offsets(ctx, enable):
