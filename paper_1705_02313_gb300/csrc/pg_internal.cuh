@@ -22,6 +22,8 @@ namespace pg {
 constexpr int kBlock = 256;
 constexpr int kWalkCap = 64;          // steps of a direct nearest-greater walk before pointer jumping takes over
 constexpr int kWalkShort = 8;         // steps of the first walk pass; longer walks continue in a dense second pass
+constexpr int kJumpFollow = 32;       // resolved vertices a pointer-jumping round may pass through at once
+constexpr int kJumpRoundsDeep = 4096; // extra pointer-jumping rounds allowed on the ruling-set path
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
 constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
 // Count-vector mode (repeated priorities): at most kMaxLevels distinct
@@ -140,6 +142,7 @@ struct pg_ctx {
     bool wide_offsets = false;  // batches take 64-bit edge offsets at any size (else from 2^31 edges)
     int32_t deep_cut = 64;      // a g-chain walk longer than this switches the game to the ruling-set ranks
     int32_t ruler_bits = 5;     // the ruling set takes about one list element in 2^ruler_bits as a ruler
+    bool deep_fallback = true;  // a deep forest or unfinished jumping hands over to the ruling-set path
     cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
 

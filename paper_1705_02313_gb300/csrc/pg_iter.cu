@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
 __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict__ plist, uint64_t* gd,
                                                       uint32_t* gd32, const int32_t* __restrict__ vgame,
                                                       const int32_t* __restrict__ gsink, int32_t sink0, Counters* cnt,
-                                                      int32_t cap) {
+                                                      int32_t cap, int cap_deep) {
     const int32_t np = cnt->n_pending;
     if (np == 0) return;
     for (int32_t r = 0;; ++r) {
@@ -141,13 +141,21 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
             if (gd_resolved(w)) continue;
             int32_t x = gd_ptr(w);
             uint64_t wx = ld_cg(gd + x);
+            uint64_t pre = gd_dist(w);  // walk length from v to x
+            // through up to kJumpFollow resolved vertices below v at once: their g-chains rise, so a long
+            // increasing run below v costs rounds / kJumpFollow instead of one round per vertex
+            for (int f = 0; f < kJumpFollow && gd_resolved(wx) && !gd_none(wx) && gd_ptr(wx) < v; ++f) {
+                pre += gd_dist(wx);
+                x = gd_ptr(wx);
+                wx = ld_cg(gd + x);
+            }
             uint64_t nw;
             if (gd_resolved(wx) && gd_none(wx)) {
                 // x is above its whole future and below v: so is v (same cycle)
                 nw = gd_pack(true, true, 0, gd_ptr(wx));
             } else {
                 int32_t y = gd_ptr(wx);
-                uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
+                uint64_t nd = pre + gd_dist(wx);
                 if (nd > kDistMax) nd = kDistMax;  // only reachable around cycles, where dist is unused
                 if (y > v) {
                     nw = gd_pack(true, false, (uint32_t)nd, y, y == sink_of(v, vgame, gsink, sink0));
@@ -168,8 +176,11 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
             if (blockIdx.x == 0 && threadIdx.x == 0) cnt->jump_rounds = r + 1;
             return;
         }
-        if (r + 1 >= cap) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cnt->err, kErrJumpRounds);
+        if (r + 1 >= cap) {  // the ruling-set path retries with a larger cap, or the call fails
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                if (cap_deep) cnt->deep = 1;
+                else atomicOr(&cnt->err, kErrJumpRounds);
+            }
             return;
         }
     }
@@ -246,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
 __global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restrict__ plist, uint32_t* gd32,
                                                         const int32_t* __restrict__ vgame,
                                                         const int32_t* __restrict__ gsink, int32_t sink0,
-                                                        Counters* cnt, int32_t cap) {
+                                                        Counters* cnt, int32_t cap, int cap_deep) {
     const int32_t np = cnt->n_pending;
     if (np == 0) return;
     for (int32_t r = 0;; ++r) {
@@ -256,8 +267,12 @@ __global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restric
             const int32_t v = plist[i];
             const uint32_t w = __ldcg(gd32 + v);
             if (!g32_pending(w)) continue;
-            const int32_t x = g32_ptr(w);
-            const uint32_t wx = __ldcg(gd32 + x);
+            int32_t x = g32_ptr(w);
+            uint32_t wx = __ldcg(gd32 + x);
+            for (int f = 0; f < kJumpFollow && !(wx & kG32Pend) && g32_ptr(wx) < v; ++f) {  // resolved, rising
+                x = g32_ptr(wx);
+                wx = __ldcg(gd32 + x);
+            }
             uint32_t nw;
             if (g32_none(wx) && !g32_pending(wx)) {
                 // x is above its whole future and below v: so is v (same cycle)
@@ -280,8 +295,11 @@ __global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restric
             if (blockIdx.x == 0 && threadIdx.x == 0) cnt->jump_rounds = r + 1;
             return;
         }
-        if (r + 1 >= cap) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cnt->err, kErrJumpRounds);
+        if (r + 1 >= cap) {  // the iteration is abandoned and retried on the ruling-set path
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                if (cap_deep) cnt->deep = 1;
+                else atomicOr(&cnt->err, kErrJumpRounds);
+            }
             return;
         }
     }
@@ -337,7 +355,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
                                                    int32_t* __restrict__ dom, int want_dom,
                                                    const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt,
                                                    int32_t deep_cut) {
-    if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
+    if (cnt->err || cnt->deep) return;  // unfinished jumping: g-words may point downwards, no chain walk would end
     __shared__ int32_t tkey[kHotSlots], tcnt[kHotSlots];
     for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
         tkey[i] = -1;
@@ -1200,7 +1218,7 @@ __device__ inline int32_t top_id(uint32_t t) { return (int32_t)(t & 0x3fffffffu)
 __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags,
                                                      uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
                                                      GameState* gst, Counters* cnt, int32_t deep_cut) {
-    if (cnt->err) return;  // unfinished jumping: g-words may point downwards, so no chain walk would end
+    if (cnt->err || cnt->deep) return;  // unfinished jumping: g-words may point downwards, no chain walk would end
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
@@ -1531,8 +1549,11 @@ pg_status enqueue_k1(pg_game* g) {
     {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
+        // on the ruling-set path the rounds may run much longer (long increasing runs below pending walks)
+        int cap_deep = (ctx->deep_fallback && !g->deep_mode) ? 1 : 0;
+        if (g->deep_mode) cap += kJumpRoundsDeep;
         void* args[] = {(void*)&g->plist, (void*)&g->gd,    (void*)&g->gd32, (void*)&g->vgame,
-                        (void*)&g->gsink, (void*)&g->sink0, (void*)&c,       (void*)&cap};
+                        (void*)&g->gsink, (void*)&g->sink0, (void*)&c,       (void*)&cap, (void*)&cap_deep};
         prof_begin(g, KID_JUMP);
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump_coop, g->coop_blocks, kBlock, args, 0, s));
         prof_end(g, KID_JUMP, 1);
@@ -1664,8 +1685,9 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
+        int cap_deep = ctx->deep_fallback ? 1 : 0;
         void* args[] = {(void*)&g->plist, (void*)&g->gd32, (void*)&g->vgame, (void*)&g->gsink,
-                        (void*)&g->sink0, (void*)&c,       (void*)&cap};
+                        (void*)&g->sink0, (void*)&c,       (void*)&cap,      (void*)&cap_deep};
         prof_begin(g, KID_JUMP);
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump32_coop, g->coop_blocks, kBlock, args, 0, s));
         prof_end(g, KID_JUMP, 1);
