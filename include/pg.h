@@ -114,8 +114,12 @@ typedef struct {
     int32_t *val_counts; /* count-vector mode only: n x d counts (row per vertex); ignored otherwise */
 } pg_valuation;
 
-/* Context: one GPU, one stream. device is the CUDA ordinal. */
+/* Context: one GPU, one stream. device is the CUDA ordinal. pg_ctx_create
+ * loads the tuning table named by PG_TUNING_FILE, if set (pg_load_tuning). */
 pg_status pg_ctx_create(pg_ctx **out, int device);
+/* The device's name (as the CUDA runtime reports it) into buf (cap bytes,
+ * NUL-terminated, truncated to fit); used to find a device's tuning table. */
+pg_status pg_device_name(int device, char *buf, int32_t cap);
 void pg_ctx_destroy(pg_ctx *ctx);
 
 /* Orders all later work of ctx on stream (a cudaStream_t, e.g. a torch
@@ -386,23 +390,48 @@ pg_status pg_last_timing(const pg_game *game, double *total_ms, double *valuatio
  * synchronises once per iteration. Both give identical results. The paper has
  * no counterpart (it concerns launching work on the device only). */
 pg_status pg_set_graphs(pg_ctx *ctx, int32_t enable);
-/* Work partitioning of the valuation, per context (the paper has no
- * counterpart; results never depend on it):
- *   deep_cut    a g-chain walk longer than this (the play rises that many
- *               times) sends the game to the ruling-set path for the rest of
- *               the call: the Euler tour of the nearest-greater forest ranked
- *               by a sparse ruling set (Section 5's list ranking), work linear
- *               in n whatever the forest's depth; default 64;
- *   ruler_bits  the ruling set takes about one list element in 2^ruler_bits as
- *               a ruler (1..16); default 5.
- * pg_set_tuning ignores zero fields; PG_EINVAL for negative values or
- * ruler_bits > 16. */
+/* Work partitioning of the valuation (the paper has no counterpart; results
+ * never depend on it):
+ *   deep_cut      a g-chain walk longer than this (the play rises that many
+ *                 times), or pointer jumping that needs more rounds than its
+ *                 cap, sends the call to the ruling-set path: the Euler tour of
+ *                 the nearest-greater forest ranked by a sparse ruling set
+ *                 (Section 5's list ranking), work linear in n whatever the
+ *                 forest's depth; default 64;
+ *   ruler_bits    the ruling set takes about one list element in 2^ruler_bits
+ *                 as a ruler (1..16); default 5;
+ *   walk_cap      steps of a direct nearest-greater walk before pointer
+ *                 jumping takes over (16, 32, 64 or 128); default 64;
+ *   switch_block  threads per block of the switching passes that compare
+ *                 valuations (128, 256 or 512); default 256;
+ *   loop_ranks    1: loop iterations rank every valuation (pg_set_loop_ranks).
+ * pg_set_tuning sets the context's values (zero fields keep the current
+ * ones); PG_EINVAL for a value outside the ranges above. */
 typedef struct {
     int32_t deep_cut;
     int32_t ruler_bits;
+    int32_t walk_cap;
+    int32_t switch_block;
+    int32_t loop_ranks;
 } pg_tuning;
 pg_status pg_set_tuning(pg_ctx *ctx, const pg_tuning *t);
 pg_status pg_get_tuning(const pg_ctx *ctx, pg_tuning *t);
+
+/* A table of partitionings by size, as the autotuner
+ * (paper_1705_02313_gb300/tune.py) writes it: each call on a game (or batch,
+ * or server layout) of n ids uses the first entry with n <= max_ids (entries
+ * by increasing max_ids; zero fields take the defaults above), else the
+ * context's values. count = 0 clears the table. pg_load_tuning reads the table
+ * from a text file, one entry per line: "max_ids deep_cut ruler_bits walk_cap
+ * switch_block loop_ranks" ('#' starts a comment line). pg_ctx_create loads the
+ * file named by the environment variable PG_TUNING_FILE when it is set (a file
+ * that cannot be read or parsed leaves the table empty). */
+typedef struct {
+    int64_t max_ids;
+    pg_tuning t;
+} pg_tuning_entry;
+pg_status pg_set_tuning_table(pg_ctx *ctx, const pg_tuning_entry *entries, int32_t count);
+pg_status pg_load_tuning(pg_ctx *ctx, const char *path);
 
 /* Edge offsets of the packed layout of pg_solve_batch: 32-bit while the batch
  * holds fewer than 2^31 edges, 64-bit beyond. enable = 1 takes 64-bit offsets

@@ -1,5 +1,6 @@
 // C ABI of libpg: contexts, games, and the loops of Algorithm 1 (Section 4).
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -345,8 +346,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     pg_ctx* ctx = g->ctx;
     const int w = even ? 1 : 0;
     if (g->loop_exec[w] && g->loop_cap[w] == cap && g->loop_limit[w] == limit && g->loop_reset[w] == g->reset_tau &&
-        g->loop_cmp[w] == loop_compares(g) && g->loop_deep[w] == g->deep_mode && g->loop_cut[w] == ctx->deep_cut &&
-        g->loop_rbits[w] == ctx->ruler_bits)
+        g->loop_cmp[w] == loop_compares(g) && g->loop_deep[w] == g->deep_mode && g->loop_tune[w] == g->tune)
         return true;
     if (g->loop_exec[w]) {
         cudaGraphExecDestroy(g->loop_exec[w]);
@@ -414,8 +414,7 @@ bool build_loop_graph(pg_game* g, int64_t cap, bool even, int64_t limit) {
     g->loop_reset[w] = g->reset_tau;
     g->loop_cmp[w] = loop_compares(g);
     g->loop_deep[w] = g->deep_mode;
-    g->loop_cut[w] = ctx->deep_cut;
-    g->loop_rbits[w] = ctx->ruler_bits;
+    g->loop_tune[w] = g->tune;
     return true;
 }
 
@@ -500,6 +499,31 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
 
 }  // namespace pg
 
+namespace pg {
+namespace {
+// Checks t and merges its nonzero fields into out.
+bool merge_tuning(const pg_tuning& t, Tune* out) {
+    if (t.deep_cut < 0 || t.ruler_bits < 0 || t.ruler_bits > 16 || t.loop_ranks < 0 || t.loop_ranks > 1)
+        return false;
+    if (t.walk_cap && t.walk_cap != 16 && t.walk_cap != 32 && t.walk_cap != 64 && t.walk_cap != 128) return false;
+    if (t.switch_block && t.switch_block != 128 && t.switch_block != 256 && t.switch_block != 512) return false;
+    if (t.deep_cut) out->deep_cut = t.deep_cut;
+    if (t.ruler_bits) out->ruler_bits = t.ruler_bits;
+    if (t.walk_cap) out->walk_cap = t.walk_cap;
+    if (t.switch_block) out->switch_block = t.switch_block;
+    out->loop_ranks = t.loop_ranks;
+    return true;
+}
+}  // namespace
+
+Tune tune_for(const pg_ctx* ctx, int64_t n) {
+    for (const Tune& t : ctx->tune_table)
+        if (n <= t.max_ids) return t;
+    return ctx->tune;
+}
+
+}  // namespace pg
+
 using namespace pg;
 
 extern "C" {
@@ -516,7 +540,17 @@ pg_status pg_ctx_create(pg_ctx** out, int device) {
         delete c;
         return PG_ENOMEM;
     }
+    const char* tf = getenv("PG_TUNING_FILE");  // the autotuner's table, when the caller names one
+    if (tf && *tf && pg_load_tuning(c, tf) != PG_OK) c->tune_table.clear();
     *out = c;
+    return PG_OK;
+}
+
+pg_status pg_device_name(int device, char* buf, int32_t cap) {
+    if (!buf || cap < 1) return PG_EINVAL;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return PG_ECUDA;
+    snprintf(buf, (size_t)cap, "%s", p.name);
     return PG_OK;
 }
 
@@ -553,18 +587,58 @@ pg_status pg_set_graphs(pg_ctx* ctx, int32_t enable) {
 
 pg_status pg_set_tuning(pg_ctx* ctx, const pg_tuning* t) {
     if (!ctx || !t) return PG_EINVAL;
-    if (t->deep_cut < 0 || t->ruler_bits < 0 || t->ruler_bits > 16) return fail(ctx, PG_EINVAL, "pg_set_tuning: bad value");
-    if (t->deep_cut) ctx->deep_cut = t->deep_cut;
-    if (t->ruler_bits) ctx->ruler_bits = t->ruler_bits;
+    Tune x = ctx->tune;
+    pg_tuning u = *t;
+    if (!u.loop_ranks) u.loop_ranks = ctx->tune.loop_ranks;  // zero keeps it, like the other fields
+    if (!merge_tuning(u, &x)) return fail(ctx, PG_EINVAL, "pg_set_tuning: bad value");
+    ctx->tune = x;
     return PG_OK;
 }
 
 pg_status pg_get_tuning(const pg_ctx* ctx, pg_tuning* t) {
     if (!ctx || !t) return PG_EINVAL;
-    *t = pg_tuning{};
-    t->deep_cut = ctx->deep_cut;
-    t->ruler_bits = ctx->ruler_bits;
+    *t = pg_tuning{ctx->tune.deep_cut, ctx->tune.ruler_bits, ctx->tune.walk_cap, ctx->tune.switch_block,
+                   ctx->tune.loop_ranks};
     return PG_OK;
+}
+
+pg_status pg_set_tuning_table(pg_ctx* ctx, const pg_tuning_entry* e, int32_t count) {
+    if (!ctx || count < 0 || (count && !e)) return PG_EINVAL;
+    std::vector<Tune> table;
+    for (int32_t i = 0; i < count; ++i) {
+        Tune x;  // the defaults, then the entry's nonzero fields
+        if (e[i].max_ids < 1 || (i && e[i].max_ids <= e[i - 1].max_ids) || !merge_tuning(e[i].t, &x))
+            return fail(ctx, PG_EINVAL, "pg_set_tuning_table: bad entry (max_ids must increase)");
+        x.max_ids = e[i].max_ids;
+        table.push_back(x);
+    }
+    ctx->tune_table = table;
+    return PG_OK;
+}
+
+pg_status pg_load_tuning(pg_ctx* ctx, const char* path) {
+    if (!ctx || !path) return PG_EINVAL;
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(ctx, PG_EINVAL, "pg_load_tuning: cannot open the file");
+    std::vector<pg_tuning_entry> es;
+    char line[512];
+    bool bad = false;
+    while (fgets(line, sizeof line, f)) {
+        const char* p = line;
+        while (*p == ' ' || *p == '\t') ++p;
+        if (*p == '#' || *p == '\n' || *p == '\0') continue;
+        long long m = 0;
+        int a = 0, b = 0, c = 0, d = 0, r = 0;
+        if (sscanf(p, "%lld %d %d %d %d %d", &m, &a, &b, &c, &d, &r) != 6) {
+            bad = true;
+            break;
+        }
+        es.push_back(pg_tuning_entry{(int64_t)m, pg_tuning{a, b, c, d, r}});
+    }
+    fclose(f);
+    if (bad) return fail(ctx, PG_EINVAL, "pg_load_tuning: a line is not 'max_ids deep_cut ruler_bits walk_cap "
+                                         "switch_block loop_ranks'");
+    return pg_set_tuning_table(ctx, es.data(), (int32_t)es.size());
 }
 
 pg_status pg_set_wide_offsets(pg_ctx* ctx, int32_t enable) {
@@ -575,7 +649,7 @@ pg_status pg_set_wide_offsets(pg_ctx* ctx, int32_t enable) {
 
 pg_status pg_set_loop_ranks(pg_ctx* ctx, int32_t enable) {
     if (!ctx) return PG_EINVAL;
-    ctx->loop_ranks = enable != 0;
+    ctx->tune.loop_ranks = enable != 0;
     return PG_OK;
 }
 

@@ -655,7 +655,7 @@ namespace pg {
 pg_status prepare_deep(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     const int64_t n = g->n;
-    const int bits = std::max(1, std::min(ctx->ruler_bits, 16));
+    const int bits = std::max(1, std::min(g->tune.ruler_bits, 16));
     // rulers: list heads plus about 2n / 2^bits hashed ones, with room for twice that
     const int64_t want = 2 * ((2 * n) >> bits) + g->ngames + 1024;
     const int32_t rcap = (int32_t)std::min<int64_t>(want, 2 * n + g->ngames + 1024);
@@ -740,7 +740,7 @@ pg_status enqueue_valuation_deep(pg_game* g, bool want_dom) {
     k_deep_links_slot<<<gg, kBlock, 0, s>>>(g->ngames, g->d_podd, g->d_peven, g->d_oddL, g->d_evenL, g->gsink,
                                             g->sink0, g->vgame ? 0 : 1, g->d_nxt, g->d_wt, vis, c);
     // D4
-    const int bits = std::max(1, std::min(ctx->ruler_bits, 16));
+    const int bits = std::max(1, std::min(g->tune.ruler_bits, 16));
     k_deep_rulers<<<grid_for(2 * (int64_t)n), kBlock, 0, s>>>(n, g->kind, bits, g->d_rcap, g->d_rid, g->d_rl, g->d_own,
                                                               c);
     int2* val0 = g->d_val;

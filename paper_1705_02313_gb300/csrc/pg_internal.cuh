@@ -126,6 +126,20 @@ cudaError_t exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, void* 
 cudaError_t exclusive_popc_scan(const uint32_t* words, int32_t* out, int64_t nwords, void* tmp,
                                 size_t tmp_bytes, cudaStream_t s);
 
+// Work partitioning of the valuation (pg_set_tuning). Results never depend on it.
+struct Tune {
+    int64_t max_ids = INT64_MAX;  // a table entry applies to games (batches) of at most this many ids
+    int32_t deep_cut = 64;        // a g-chain walk longer than this switches the call to the ruling-set ranks
+    int32_t ruler_bits = 5;       // the ruling set takes about one list element in 2^ruler_bits as a ruler
+    int32_t walk_cap = kWalkCap;  // steps of a direct nearest-greater walk before pointer jumping (16..128)
+    int32_t switch_block = kBlock;// threads per block of the compare-mode switching passes (128, 256, 512)
+    int32_t loop_ranks = 0;       // loop iterations rank every valuation (else they only compare them)
+    bool operator==(const Tune& o) const {
+        return deep_cut == o.deep_cut && ruler_bits == o.ruler_bits && walk_cap == o.walk_cap &&
+               switch_block == o.switch_block && loop_ranks == o.loop_ranks;
+    }
+};
+
 }  // namespace pg
 
 // Library objects
@@ -138,10 +152,9 @@ struct pg_ctx {
     int64_t launches = 0;       // kernels launched through this context
     bool quiet = false;         // record no error message (keeps failing calls free of host allocation)
     bool graphs = true;         // run the iteration loop as one CUDA graph with a device-side condition
-    bool loop_ranks = false;    // loop iterations rank every valuation (else they only compare them)
     bool wide_offsets = false;  // batches take 64-bit edge offsets at any size (else from 2^31 edges)
-    int32_t deep_cut = 64;      // a g-chain walk longer than this switches the game to the ruling-set ranks
-    int32_t ruler_bits = 5;     // the ruling set takes about one list element in 2^ruler_bits as a ruler
+    pg::Tune tune;              // partitioning of games beyond every table entry (pg_set_tuning)
+    std::vector<pg::Tune> tune_table;  // by increasing max_ids (pg_set_tuning_table, pg_load_tuning)
     bool deep_fallback = true;  // a deep forest or unfinished jumping hands over to the ruling-set path
     cudaStream_t cap_stream = nullptr;  // private stream on which loop graphs are captured
 };
@@ -269,8 +282,8 @@ struct pg_game {
     bool loop_reset[2] = {false, false};  // the SI-Reset setting each loop graph was built with
     bool loop_cmp[2] = {false, false};    // each loop graph compares valuations (loop_compares)
     bool loop_deep[2] = {false, false};   // each loop graph ranks through the ruling-set path
-    int32_t loop_cut[2] = {0, 0};         // the cutover depth each loop graph was built with
-    int32_t loop_rbits[2] = {0, 0};       // the ruler stride each loop graph was built with
+    pg::Tune loop_tune[2];                // the partitioning each loop graph was built with
+    pg::Tune tune;                        // the partitioning of the current call (tune_for, at its start)
     // timing of the last call
     double t_total = 0, t_val = 0, t_switch = 0;
     int64_t t_vals = 0;
@@ -285,6 +298,8 @@ struct pg_game {
 
 // internal entry points shared by the translation units
 namespace pg {
+// The partitioning for a game (batch) of n ids: the first table entry covering n, else the context's.
+Tune tune_for(const pg_ctx* ctx, int64_t n);
 pg_status fail(pg_ctx* ctx, pg_status code, const char* msg);
 pg_status cuda_fail(pg_ctx* ctx, cudaError_t e, const char* where);
 pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off, const int32_t* tgt,

@@ -1344,8 +1344,8 @@ __device__ inline int cmp_sink(uint32_t tu) {
 // both are TOP, so Odd switches when its best successor differs from the
 // current one and is finite, Even when they differ and the current one is not
 // TOP (the best one is then at least as good as TOP only if equal to it).
-template <typename OffT>
-__global__ void __launch_bounds__(kBlock) k_switch_cmp(int32_t n, int player, const OffT* __restrict__ off,
+template <typename OffT, int BS>
+__global__ void __launch_bounds__(BS) k_switch_cmp(int32_t n, int player, const OffT* __restrict__ off,
                                                        const int32_t* __restrict__ tgt,
                                                        const uint8_t* __restrict__ flags,
                                                        const uint32_t* __restrict__ gd32,
@@ -1521,6 +1521,7 @@ pg_status reset_scratch(pg_game* g) {
     pg_ctx* ctx = g->ctx;
     g->deep_mode = false;  // every call starts on the default path; a deep g-forest switches it
     g->val_deep = false;
+    g->tune = tune_for(ctx, g->n);
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(g->sz, 0, sizeof(int32_t) * n, s));
@@ -1543,8 +1544,17 @@ pg_status enqueue_k1(pg_game* g) {
     Counters* c = g->cnt;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd,
-                                                    g->gd32, g->plist, g->sz, g->oddsz, c, &c->n_pending);
+    {
+        auto walk = k_walk<kWalkCap>;
+        switch (g->tune.walk_cap) {
+            case 16: walk = k_walk<16>; break;
+            case 32: walk = k_walk<32>; break;
+            case 128: walk = k_walk<128>; break;
+            default: break;
+        }
+        walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd, g->gd32,
+                                            g->plist, g->sz, g->oddsz, c, &c->n_pending);
+    }
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;
@@ -1580,7 +1590,7 @@ pg_status enqueue_valuation(pg_game* g, bool want_dom) {
     const unsigned c1grid =
         (g->chain1_blocks > 0 && !g->vgame) ? std::min(ilp_grid(n), (unsigned)g->chain1_blocks) : ilp_grid(n);
     k_chain1<<<c1grid, kBlock, 0, s>>>(n, g->gd32, g->flags, g->pri, g->sz, g->ccnt, g->slot, g->kind, g->cls,
-                                       g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c, ctx->deep_cut);
+                                       g->dom, want_dom ? 1 : 0, g->vgame, g->gst, c, g->tune.deep_cut);
     prof_end(g, KID_CHAIN1, 1);
     prof_begin(g, KID_CSCAN);
     PG_CUDA_TRY(ctx, exclusive_scan_i32(g->ccnt, g->coff, (int64_t)n + 1, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
@@ -1670,7 +1680,7 @@ pg_status enqueue_reset(pg_game* g) {
     return PG_OK;
 }
 
-bool loop_compares(const pg_game* g) { return !g->cv && !g->ctx->loop_ranks && !g->deep_mode; }
+bool loop_compares(const pg_game* g) { return !g->cv && !g->tune.loop_ranks && !g->deep_mode; }
 
 pg_status enqueue_valuation_cmp(pg_game* g) {
     pg_ctx* ctx = g->ctx;
@@ -1679,8 +1689,17 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     Counters* c = g->cnt;
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
-    k_walk_cmp<kWalkCap><<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32,
-                                                        g->plist, &c->n_pending);
+    {
+        auto walk = k_walk_cmp<kWalkCap>;
+        switch (g->tune.walk_cap) {
+            case 16: walk = k_walk_cmp<16>; break;
+            case 32: walk = k_walk_cmp<32>; break;
+            case 128: walk = k_walk_cmp<128>; break;
+            default: break;
+        }
+        walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32, g->plist,
+                                            &c->n_pending);
+    }
     prof_end(g, KID_WALK, 1);
     {
         int32_t cap = 64;
@@ -1695,11 +1714,32 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     prof_begin(g, KID_CLASSIFY);
     // the top words live in the chain-weight array, which only a full valuation uses
     k_classify<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame, g->gst, c,
-                                              ctx->deep_cut);
+                                              g->tune.deep_cut);
     prof_end(g, KID_CLASSIFY, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
 }
+
+namespace {
+template <int BS>
+void launch_switch_cmp_bs(pg_game* g, int player) {
+    const int64_t b = std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + BS - 1) / BS, 152LL * 64 * kBlock / BS));
+    cudaStream_t s = g->ctx->stream;
+    const uint32_t* topw = (const uint32_t*)g->wgt;
+    if (g->off64)
+        k_switch_cmp<int64_t, BS><<<(unsigned)b, BS, 0, s>>>(g->n, player, g->off64, g->tgt, g->flags, g->gd32, topw,
+                                                             g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+    else
+        k_switch_cmp<int32_t, BS><<<(unsigned)b, BS, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->gd32, topw,
+                                                             g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+}
+
+void launch_switch_cmp(pg_game* g, int player, int bs) {
+    if (bs == 128) launch_switch_cmp_bs<128>(g, player);
+    else if (bs == 512) launch_switch_cmp_bs<512>(g, player);
+    else launch_switch_cmp_bs<256>(g, player);
+}
+}  // namespace
 
 pg_status enqueue_switch_cmp(pg_game* g, int player) {
     pg_ctx* ctx = g->ctx;
@@ -1707,12 +1747,7 @@ pg_status enqueue_switch_cmp(pg_game* g, int player) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(&g->cnt->n_switch, 0, sizeof(int32_t), s));
     int kid = player ? KID_SWITCH_ODD : KID_SWITCH_EVEN;
     prof_begin(g, kid);
-    if (g->off64)
-        k_switch_cmp<int64_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off64, g->tgt, g->flags, g->gd32,
-                                                                (const uint32_t*)g->wgt, g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
-    else
-        k_switch_cmp<int32_t><<<grid_for(g->n), kBlock, 0, s>>>(g->n, player, g->off, g->tgt, g->flags, g->gd32,
-                                                                (const uint32_t*)g->wgt, g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
+    launch_switch_cmp(g, player, g->tune.switch_block);
     prof_end(g, kid, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;

@@ -150,7 +150,7 @@ extern "C" pg_status pg_valuate_static(int32_t n, const int32_t* succ, const uin
     ctx.device = device;
     ctx.stream = (cudaStream_t)stream;
     ctx.quiet = true;
-    ctx.deep_cut = INT32_MAX;  // no ruling-set path here (its scratch is not in the fixed array)
+    ctx.tune.deep_cut = INT32_MAX;  // no ruling-set path here (its scratch is not in the fixed array)
     ctx.deep_fallback = false;
     unsigned char* base = nullptr;
     int coop = 0, chain1 = 0;

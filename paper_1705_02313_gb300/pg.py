@@ -63,8 +63,15 @@ class pg_server_opts(C.Structure):
                 ("round_iters", C.c_int32), ("max_inner", C.c_int64), ("wide_offsets", C.c_int32)]
 
 
+TUNING_FIELDS = ("deep_cut", "ruler_bits", "walk_cap", "switch_block", "loop_ranks")
+
+
 class pg_tuning(C.Structure):
-    _fields_ = [("deep_cut", C.c_int32), ("ruler_bits", C.c_int32)]
+    _fields_ = [(f, C.c_int32) for f in TUNING_FIELDS]
+
+
+class pg_tuning_entry(C.Structure):
+    _fields_ = [("max_ids", C.c_int64), ("t", pg_tuning)]
 
 
 class pg_served(C.Structure):
@@ -122,6 +129,9 @@ def lib():
     L.pg_set_wide_offsets.argtypes = [P, I32]
     L.pg_set_tuning.argtypes = [P, C.POINTER(pg_tuning)]
     L.pg_get_tuning.argtypes = [P, C.POINTER(pg_tuning)]
+    L.pg_set_tuning_table.argtypes = [P, C.POINTER(pg_tuning_entry), I32]
+    L.pg_load_tuning.argtypes = [P, C.c_char_p]
+    L.pg_device_name.argtypes = [C.c_int, C.c_char_p, I32]
     L.pg_release_cached_memory.argtypes = [C.c_int]
     L.pg_last_loop.argtypes = [P, C.POINTER(I32), C.POINTER(I64)]
     L.pg_last_timing.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -141,7 +151,7 @@ def lib():
     L.pg_reset_stats.argtypes = [P]
     L.pg_launch_count.argtypes = [P, C.POINTER(I64)]
     for name in ["pg_solve_batch", "pg_valuate_static", "pg_kernel_stats", "pg_reset_stats", "pg_launch_count", "pg_ctx_create", "pg_set_stream", "pg_load_csr", "pg_game_info", "pg_game_dummies", "pg_solve",
-                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_set_wide_offsets", "pg_set_tuning", "pg_get_tuning", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
+                 "pg_best_response", "pg_valuate", "pg_set_timing", "pg_last_timing", "pg_set_graphs", "pg_set_loop_ranks", "pg_set_wide_offsets", "pg_set_tuning", "pg_get_tuning", "pg_set_tuning_table", "pg_load_tuning", "pg_device_name", "pg_last_loop", "pg_release_cached_memory", "pg_server_create", "pg_server_submit", "pg_server_poll",
                  "pg_server_fetch", "pg_server_get_stats", "pg_game_levels", "pg_game_counters", "pg_best_response_bf"]:
         getattr(L, name).restype = I32
     _lib = L
@@ -198,11 +208,29 @@ def _dtype_check(x, np_dtype, name):
 # ---------------------------------------------------------------------------
 # entry points (same names as include/pg.h)
 
-def pg_ctx_create(device=0):
+def pg_device_name(device=0):
+    buf = C.create_string_buffer(256)
+    rc = lib().pg_device_name(int(device), buf, 256)
+    if rc != PG_OK:
+        raise PgError(rc, "pg_device_name")
+    return buf.value.decode(errors="replace")
+
+
+def pg_ctx_create(device=0, tuning=True):
+    """A context on ``device``. With tuning (and no PG_TUNING_FILE, which the
+    library itself loads) the autotuner's table for this device model is
+    loaded when the package holds one (tuning/<device>.txt, see tune.py)."""
     h = C.c_void_p()
     rc = lib().pg_ctx_create(C.byref(h), device)
     if rc != PG_OK:
         raise PgError(rc, "pg_ctx_create(%d) failed" % device)
+    if tuning and not os.environ.get("PG_TUNING_FILE"):
+        from . import tune
+        path = tune.default_table_path(pg_device_name(device))
+        if os.path.exists(path):
+            pg_load_tuning(h, path)
+    elif not tuning:
+        pg_set_tuning_table(h, [])
     return h
 
 
@@ -477,16 +505,29 @@ def pg_set_graphs(ctx, enable):
     _check(ctx, lib().pg_set_graphs(ctx, 1 if enable else 0), "pg_set_graphs")
 
 
-def pg_set_tuning(ctx, deep_cut=0, ruler_bits=0):
+def pg_set_tuning(ctx, deep_cut=0, ruler_bits=0, walk_cap=0, switch_block=0, loop_ranks=0):
     """Sets the work partitioning of the valuation (zero keeps a value)."""
-    t = pg_tuning(int(deep_cut), int(ruler_bits))
+    t = pg_tuning(int(deep_cut), int(ruler_bits), int(walk_cap), int(switch_block), int(loop_ranks))
     _check(ctx, lib().pg_set_tuning(ctx, C.byref(t)), "pg_set_tuning")
 
 
 def pg_get_tuning(ctx):
     t = pg_tuning()
     _check(ctx, lib().pg_get_tuning(ctx, C.byref(t)), "pg_get_tuning")
-    return {"deep_cut": t.deep_cut, "ruler_bits": t.ruler_bits}
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+
+def pg_set_tuning_table(ctx, entries):
+    """entries: [(max_ids, {field: value})] by increasing max_ids; [] clears."""
+    arr = (pg_tuning_entry * max(len(entries), 1))()
+    for i, (m, d) in enumerate(entries):
+        arr[i].max_ids = int(m)
+        arr[i].t = pg_tuning(*[int(d.get(f, 0)) for f in TUNING_FIELDS])
+    _check(ctx, lib().pg_set_tuning_table(ctx, arr, len(entries)), "pg_set_tuning_table")
+
+
+def pg_load_tuning(ctx, path):
+    _check(ctx, lib().pg_load_tuning(ctx, str(path).encode()), "pg_load_tuning")
 
 
 def pg_set_wide_offsets(ctx, enable):

@@ -34,7 +34,7 @@ def pg():
 
 @pytest.fixture
 def ctx(pg):
-    c = pg.pg_ctx_create(0)
+    c = pg.pg_ctx_create(0, tuning=False)
     yield c
     pg.pg_ctx_destroy(c)
 
@@ -126,7 +126,8 @@ def test_deep_chains_take_the_ruling_set_path(pg, ctx, n, run, cycles, deep):
 @pytest.mark.parametrize("ruler_bits", [1, 5, 9])
 def test_tree_shapes_forced_through_the_ruling_set(pg, ctx, ruler_bits):
     pg.pg_set_tuning(ctx, deep_cut=1, ruler_bits=ruler_bits)
-    assert pg.pg_get_tuning(ctx) == {"deep_cut": 1, "ruler_bits": ruler_bits}
+    t = pg.pg_get_tuning(ctx)
+    assert (t["deep_cut"], t["ruler_bits"]) == (1, ruler_bits)
     rng = np.random.default_rng(10 + ruler_bits)
     trees = [
         shapes.build_tree([[40], [1, 3, 20, 33], [0, 2, 9, 50], [0, 1, 4]], rng),   # small, mid segments
@@ -222,8 +223,9 @@ def test_batch_forced_through_the_ruling_set(pg, ctx):
 
 def test_tuning_arguments(pg, ctx):
     before = pg.pg_get_tuning(ctx)
-    assert before == {"deep_cut": 64, "ruler_bits": 5}
-    for bad in (dict(deep_cut=-1), dict(ruler_bits=17), dict(ruler_bits=-2)):
+    assert before == {"deep_cut": 64, "ruler_bits": 5, "walk_cap": 64, "switch_block": 256, "loop_ranks": 0}
+    for bad in (dict(deep_cut=-1), dict(ruler_bits=17), dict(ruler_bits=-2), dict(walk_cap=48),
+                dict(switch_block=64)):
         with pytest.raises(pg.PgError) as e:
             pg.pg_set_tuning(ctx, **bad)
         assert e.value.code == pg.PG_EINVAL
