@@ -90,7 +90,8 @@ void free_game(pg_game* g) {
                     g->sinkval, g->wgt,  g->oddsz, g->key,   g->cls,   g->depth,   g->dom,     g->hugelist,
                     g->tiles, g->tsum,   g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128,
                     g->d_anc, g->d_sc, g->d_podd, g->d_peven, g->d_oddL, g->d_evenL, g->d_nxt, g->d_wt, g->d_loc,
-                    g->d_own, g->d_rid, g->d_rl, g->d_val, g->d_rnx};
+                    g->d_own, g->d_rid, g->d_rl, g->d_val, g->d_rnx, g->pl_vid[0], g->pl_vid[1], g->pl_off[0],
+                    g->pl_off[1], g->pl_tgt[0], g->pl_tgt[1]};
     int prev = -1;
     const bool switched =
         cudaGetDevice(&prev) == cudaSuccess && prev != g->device && cudaSetDevice(g->device) == cudaSuccess;
@@ -481,6 +482,10 @@ pg_status run_loop_once(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t l
 // game continues from the same profile with the ruling-set ranks (for the
 // rest of this call), so the trajectory is unchanged.
 pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit) {
+    if (loop_compares(g) && !g->pl_ok) {
+        pg_status st = build_player_split(g);
+        if (st) return st;
+    }
     int64_t done = 0;
     for (;;) {
         int64_t ran = 0;

@@ -259,6 +259,14 @@ struct pg_game {
     int64_t loop_klaunch[2][pg::KID_COUNT] = {};      // per kernel class
     bool last_graph = false;     // the last loop ran as a graph
     bool last_cmp = false;       // the last loop compared valuations: key, cls and depth are not the current ones
+    // the switching player's view (built before the first loop that compares valuations): for p = 0
+    // (Even, dummies included) and 1 (Odd) the ids of p's vertices in increasing order and their edge
+    // lists, contiguous (int32 offsets; not built for layouts with 64-bit offsets)
+    bool pl_ok = false;
+    int32_t* pl_vid[2] = {nullptr, nullptr};
+    int32_t* pl_off[2] = {nullptr, nullptr};
+    int32_t* pl_tgt[2] = {nullptr, nullptr};
+    int64_t pl_n[2] = {0, 0};
     // ruling-set ranks (pg_deep.cu), for games whose g-forest is deep
     bool deep_mode = false;      // every valuation of the current call takes the ruling-set path
     bool val_deep = false;       // the last valuation took it (its depths are written; no depth pass)
@@ -377,6 +385,8 @@ pg_status enqueue_valuation_cmp(pg_game* g);
 pg_status enqueue_switch_cmp(pg_game* g, int player);
 // After a loop that compared valuations: the full valuation of the current profile (key, cls, depth).
 pg_status finish_loop(pg_game* g);
+// Builds the switching players' views (pl_*) if they are missing; not under stream capture.
+pg_status build_player_split(pg_game* g);
 // K1 alone (counters cleared, nearest-greater walks and pointer jumping with walk lengths).
 pg_status enqueue_k1(pg_game* g);
 // The valuation through the ruling-set ranks of an Euler tour (pg_deep.cu): cls, depth, key, dom.

@@ -1419,6 +1419,117 @@ __global__ void __launch_bounds__(BS) k_switch_cmp(int32_t n, int player, const 
     }
 }
 
+// The switching players' views: the vertices of one player in increasing
+// id order with their edge lists copied contiguously, so that a switching
+// pass reads only its player's edges and every lane of a warp has a vertex.
+__global__ void __launch_bounds__(kBlock) k_pl_mark(int32_t n, const uint8_t* __restrict__ flags,
+                                                    uint8_t* __restrict__ m0, uint8_t* __restrict__ m1) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint8_t f = flags[v];
+        const bool vert = !(f & kSinkSlot);
+        m0[v] = vert && !(f & kOwnerOdd);
+        m1[v] = vert && (f & kOwnerOdd);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pl_gather(int32_t n, const uint8_t* __restrict__ m,
+                                                      const int32_t* __restrict__ pos,
+                                                      const int32_t* __restrict__ off, int32_t* __restrict__ vid,
+                                                      int32_t* __restrict__ deg) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (!m[v]) continue;
+        const int32_t i = pos[v];
+        vid[i] = v;
+        deg[i] = off[v + 1] - off[v];
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pl_copy(int32_t np, const int32_t* __restrict__ vid,
+                                                    const int32_t* __restrict__ off, const int32_t* __restrict__ tgt,
+                                                    const int32_t* __restrict__ poff, int32_t* __restrict__ ptgt) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const int32_t v = vid[i];
+        const int32_t e0 = off[v], k = off[v + 1] - e0, d0 = poff[i];
+        for (int32_t j = 0; j < k; ++j) ptgt[d0 + j] = tgt[e0 + j];
+    }
+}
+
+// k_switch_cmp over a player's view: thread i takes the player's i-th vertex.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_switch_cmp_pl(int32_t np, int player, const int32_t* __restrict__ vid,
+                                                      const int32_t* __restrict__ poff,
+                                                      const int32_t* __restrict__ ptgt,
+                                                      const uint8_t* __restrict__ flags,
+                                                      const uint32_t* __restrict__ gd32,
+                                                      const uint32_t* __restrict__ topw,
+                                                      const int32_t* __restrict__ vgame,
+                                                      const int32_t* __restrict__ gsink, int32_t sink0,
+                                                      GameState* gst, int32_t* strat, Counters* cnt) {
+    if (cnt->err || cnt->deep) return;  // unfinished jumping, or a deep forest (the loop stops)
+    if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
+        const GameState st = gst[0];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
+    }
+    int32_t nsw = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const int32_t v = vid[i];
+        const int32_t gi = vgame ? vgame[v] : 0;
+        if (vgame) {
+            const GameState st = gst[gi];
+            if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) continue;
+        }
+        const int32_t e0 = poff[i], e1 = poff[i + 1];
+        const int32_t cur = strat[v];
+        const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : -1;
+        int32_t best = sk;  // Even: the sink first; Odd: none yet
+        uint32_t tbest = 0;
+        bool cur_top = false;
+        for (int32_t e = e0; e < e1; e += 4) {
+            int32_t t[4];
+            uint32_t tt[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? ptgt[e + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tt[j] = t[j] >= 0 ? topw[t[j]] : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (t[j] < 0) continue;
+                if (t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
+                bool take;
+                if (player == 1) take = best < 0 || cmp_val(t[j], tt[j], best, tbest, gd32, flags) < 0;
+                else take = (best == sk ? cmp_sink(tt[j]) : cmp_val(t[j], tt[j], best, tbest, gd32, flags)) > 0;
+                if (take) {
+                    best = t[j];
+                    tbest = tt[j];
+                }
+            }
+        }
+        const bool sw = best != cur && (player == 0 ? !cur_top : !(tbest & kG32Top));
+        if (sw) {
+            strat[v] = best;
+            ++nsw;
+            if (vgame) {  // one count per group of lanes of the same game
+                cg::coalesced_group swg = cg::coalesced_threads();
+                cg::coalesced_group same = cg::labeled_partition(swg, gi);
+                if (same.thread_rank() == 0)
+                    atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+            }
+        }
+    }
+    block_add(nsw, &cnt->n_switch);
+    if (!vgame) {  // one game: the block totals are the game's
+        __shared__ int32_t tot;
+        if (threadIdx.x == 0) tot = 0;
+        __syncthreads();
+        int32_t x = nsw;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&tot, x);
+        __syncthreads();
+        if (threadIdx.x == 0 && tot) atomicAdd(player ? &gst[0].sw_odd : &gst[0].sw_even, tot);
+    }
+}
+
 }  // namespace
 
 const char* const kKernelNames[KID_COUNT] = {"walk",     "jump",      "chain1", "child_scan", "scatter",
@@ -1723,9 +1834,17 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
 namespace {
 template <int BS>
 void launch_switch_cmp_bs(pg_game* g, int player) {
-    const int64_t b = std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + BS - 1) / BS, 152LL * 64 * kBlock / BS));
     cudaStream_t s = g->ctx->stream;
     const uint32_t* topw = (const uint32_t*)g->wgt;
+    if (g->pl_ok) {  // the player's view
+        const int64_t np = g->pl_n[player];
+        const int64_t b = std::max<int64_t>(1, std::min<int64_t>((np + BS - 1) / BS, 152LL * 64 * kBlock / BS));
+        k_switch_cmp_pl<BS><<<(unsigned)b, BS, 0, s>>>((int32_t)np, player, g->pl_vid[player], g->pl_off[player],
+                                                       g->pl_tgt[player], g->flags, g->gd32, topw, g->vgame, g->gsink,
+                                                       g->sink0, g->gst, g->strat, g->cnt);
+        return;
+    }
+    const int64_t b = std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + BS - 1) / BS, 152LL * 64 * kBlock / BS));
     if (g->off64)
         k_switch_cmp<int64_t, BS><<<(unsigned)b, BS, 0, s>>>(g->n, player, g->off64, g->tgt, g->flags, g->gd32, topw,
                                                              g->vgame, g->gsink, g->sink0, g->gst, g->strat, g->cnt);
@@ -1768,6 +1887,48 @@ pg_status full_valuation(pg_game* g, bool want_dom) {
     st = enqueue_valuation_deep(g, want_dom);
     if (!st) st = sync_counters(g);
     return st;
+}
+
+pg_status build_player_split(pg_game* g) {
+    if (g->pl_ok || g->off64 || g->cv) return PG_OK;  // 64-bit layouts keep the unsplit passes
+    pg_ctx* ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int32_t n = g->n;
+    const unsigned grid = grid_for(n);
+    drop_loop_graphs(g);  // captured loops hold the old views' addresses
+    for (int p = 0; p < 2; ++p) {
+        if (g->pl_vid[p]) cudaFreeAsync(g->pl_vid[p], s);
+        if (g->pl_off[p]) cudaFreeAsync(g->pl_off[p], s);
+        if (g->pl_tgt[p]) cudaFreeAsync(g->pl_tgt[p], s);
+        g->pl_vid[p] = g->pl_off[p] = g->pl_tgt[p] = nullptr;
+    }
+    // the valuation's scratch is free before a loop: marks in kind and cls, positions in coff, degrees in
+    // hugelist
+    uint8_t* mark[2] = {g->kind, g->cls};
+    k_pl_mark<<<grid, kBlock, 0, s>>>(n, g->flags, mark[0], mark[1]);
+    PG_CUDA_TRY(ctx, cudaGetLastError());
+    int32_t* host = ctx->pinned;
+    for (int p = 0; p < 2; ++p) {
+        PG_CUDA_TRY(ctx, exclusive_scan_u8(mark[p], g->coff, n, g->scan_tmp, g->scan_tmp_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(host, g->coff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        const int32_t np = host[0];
+        g->pl_n[p] = np;
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_vid[p], sizeof(int32_t) * std::max(np, 1), s));
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_off[p], sizeof(int32_t) * ((size_t)np + 1), s));
+        k_pl_gather<<<grid, kBlock, 0, s>>>(n, mark[p], g->coff, g->off, g->pl_vid[p], g->hugelist);
+        PG_CUDA_TRY(ctx, exclusive_scan_i32(g->hugelist, g->pl_off[p], np, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(host, g->pl_off[p] + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        const int32_t mp = host[0];
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_tgt[p], sizeof(int32_t) * std::max(mp, 1), s));
+        k_pl_copy<<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_vid[p], g->off, g->tgt, g->pl_off[p],
+                                                               g->pl_tgt[p]);
+        PG_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    ctx->launches += 7;
+    g->pl_ok = true;
+    return PG_OK;
 }
 
 pg_status sync_counters(pg_game* g) {

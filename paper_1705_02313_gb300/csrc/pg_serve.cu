@@ -247,6 +247,7 @@ pg_status repack(pg_server* sv) {
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(g->gsink, hsink.data(), sizeof(int32_t) * hsink.size(), cudaMemcpyHostToDevice, s));
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(g->gst, hst.data(), sizeof(GameState) * hst.size(), cudaMemcpyHostToDevice, s));
     drop_loop_graphs(g);
+    g->pl_ok = false;  // the switching players' views follow the new layout
     pg_status st = reset_scratch(g);
     if (st) return st;
     // reset_scratch clears the loop states: put them back
