@@ -1838,7 +1838,12 @@ void launch_switch_cmp_bs(pg_game* g, int player) {
     const uint32_t* topw = (const uint32_t*)g->wgt;
     if (g->pl_ok) {  // the player's view
         const int64_t np = g->pl_n[player];
-        const int64_t b = std::max<int64_t>(1, std::min<int64_t>((np + BS - 1) / BS, 152LL * 64 * kBlock / BS));
+        // one wave of blocks striding over the view: the Even pass returns at once in most iterations, and a
+        // grid of one block per BS vertices would spend that time scheduling blocks
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int64_t wave = (int64_t)std::max(sms, 1) * (2048 / BS);
+        const int64_t b = std::max<int64_t>(1, std::min<int64_t>((np + BS - 1) / BS, wave));
         k_switch_cmp_pl<BS><<<(unsigned)b, BS, 0, s>>>((int32_t)np, player, g->pl_vid[player], g->pl_off[player],
                                                        g->pl_tgt[player], g->flags, g->gd32, topw, g->vgame, g->gsink,
                                                        g->sink0, g->gst, g->strat, g->cnt);
