@@ -5,8 +5,9 @@
 // Ids are ranks by (priority, input order), so the ids of one priority form
 // a range (a level) and the largest id on a cycle has the cycle's largest
 // priority. A count vector is encoded as one signed 128-bit key
-//   key(v) = sum over levels l of s_l * L_l(v) * 2^(25 l),  s_l = +1 (even), -1 (odd),
-// whose digits stay below 2^24 in magnitude (fewer than 2^24 ids), so keys
+//   key(v) = sum over levels l of s_l * L_l(v) * 2^(b l),  s_l = +1 (even), -1 (odd),
+// with digits of b = L.digit_bits bits, one more than the bit length of the
+// number of ids, so every digit stays below 2^(b-1) in magnitude and keys
 // compare exactly as valuations do under Maxdiff: the largest level whose
 // counts differ decides, more is better when its priority is even. The key is
 // a sum of per-vertex weights along the play, computed over the same
@@ -47,7 +48,7 @@ __device__ inline i128 weight_of_counts(const Levels& L, uint64_t c) {
 #pragma unroll
     for (int l = 0; l < kMaxLevels; ++l) {
         if (l >= L.n) break;
-        const i128 d = (i128)((c >> (7 * l)) & 127u) << (kDigitBits * l);
+        const i128 d = (i128)((c >> (7 * l)) & 127u) << (L.digit_bits * l);
         w += ((L.odd_mask >> l) & 1u) ? -d : d;
     }
     return w;
@@ -55,7 +56,7 @@ __device__ inline i128 weight_of_counts(const Levels& L, uint64_t c) {
 
 __device__ inline i128 weight_of(const Levels& L, int32_t v) {
     const int l = level_of(L, v);
-    const i128 w = (i128)1 << (kDigitBits * l);
+    const i128 w = (i128)1 << (L.digit_bits * l);
     return ((L.odd_mask >> l) & 1u) ? -w : w;
 }
 
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(kBlock) k_switch_cv(int32_t n, int player, con
 }
 
 // Count vectors of the original vertices (rows of nlev), decoded from the
-// keys: balanced base-2^25 digits, each the signed count of its level.
+// keys: balanced base-2^b digits (b = L.digit_bits), each the signed count of its level.
 __global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i128* __restrict__ key,
                          const uint8_t* __restrict__ cls, Levels L, int32_t* __restrict__ out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
@@ -484,10 +485,11 @@ __global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i12
         const bool fin = cls[i] == kFin;
         i128 k = fin ? key[i] : 0;
         for (int l = 0; l < L.n; ++l) {
-            // the lowest digit in (-2^24, 2^24): low 25 bits, taken negative from 2^24 up
-            int64_t a = (int64_t)(k & (i128)((1 << kDigitBits) - 1));
-            if (a >= (1ll << (kDigitBits - 1))) a -= 1ll << kDigitBits;
-            k = (k - (i128)a) >> kDigitBits;  // exact: k - a is a multiple of 2^25
+            // the lowest digit in (-2^(b-1), 2^(b-1)): low b bits, taken negative from 2^(b-1) up
+            const int b = L.digit_bits;
+            int64_t a = (int64_t)(k & (i128)((1ll << b) - 1));
+            if (a >= (1ll << (b - 1))) a -= 1ll << b;
+            k = (k - (i128)a) >> b;  // exact: k - a is a multiple of 2^b
             out[v * L.n + l] = (int32_t)(((L.odd_mask >> l) & 1u) ? -a : a);
         }
     }

@@ -27,12 +27,13 @@ constexpr int kJumpRoundsDeep = 4096; // extra pointer-jumping rounds allowed on
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
 constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
 // Count-vector mode (repeated priorities): at most kMaxLevels distinct
-// priorities; a count vector is one signed 128-bit key with one base-2^25
-// digit per level (fewer than 2^24 ids, so every digit stays below 2^24 in
-// magnitude and the key order is the order of Section 3).
+// priorities; a count vector is one signed 128-bit key with one digit of
+// Levels::digit_bits bits per level, wide enough that every signed count
+// stays below half the digit's range (so the key order is the order of
+// Section 3), and levels x digit_bits <= kKeyBits (the top key stays above
+// every finite one).
 constexpr int kMaxLevels = 5;
-constexpr int kDigitBits = 25;
-constexpr int32_t kMaxCvIds = (1 << 24) - 1;
+constexpr int kKeyBits = 126;
 
 // flags[v]
 constexpr uint8_t kOwnerOdd = 1;   // owner is Odd
@@ -179,6 +180,7 @@ struct Levels {
     int32_t n;
     uint32_t odd_mask;
     int32_t start[pg::kMaxLevels + 1];
+    int32_t digit_bits;  // bit length of the id count + 1: every count lies in (-2^(digit_bits-1), 2^(digit_bits-1))
 };
 
 // A loaded game, or a batch of games packed into one id space. Every game's

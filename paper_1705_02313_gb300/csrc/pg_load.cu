@@ -366,8 +366,6 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     if (mp > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^31-2 edges after preprocessing");
     if ((int64_t)maxpri + (cv ? 2 : 2 * (int64_t)k) > INT32_MAX - 1)
         return fail(ctx, PG_EINVAL, "pg_load_csr: priorities too large for the preprocessing shift");
-    if (cv && np + 1 > kMaxCvIds)
-        return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities need fewer than 2^24 vertices after preprocessing");
 
     pg_game* g = new pg_game();
     g->ctx = ctx;
@@ -435,6 +433,17 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
             return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities support at most 5 distinct priorities "
                                               "after preprocessing (the dummies' priority counts as one)");
         }
+        // digits: one bit more than the bit length of the ids (counts of a play never exceed them)
+        int32_t bits = 1;
+        while (bits < 40 && ((np + 1) >> bits) != 0) ++bits;
+        bits += 1;
+        if (nlev * bits > kKeyBits) {
+            free_game(g);
+            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities: levels x (bit length of the vertex "
+                                              "count + 1) must stay within 126 bits (5 priorities: fewer than 2^24 "
+                                              "vertices; 4: fewer than 2^30)");
+        }
+        g->lev.digit_bits = bits;
         uint8_t *lvl8, *ind;
         int32_t* pos;
         LG_TRY(T.get(&lvl8, np));
