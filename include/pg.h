@@ -136,8 +136,10 @@ const char *pg_last_error(const pg_ctx *ctx);
  * range, an owner other than 0/1, a negative priority, sizes beyond 2^30
  * vertices or 2^31-1 edges after preprocessing). Repeated priorities load in
  * count-vector mode (Section 5 with the count vectors of Section 3); such a
- * game returns PG_EUNSUPPORTED only beyond that mode's limits, more than 5
- * distinct priorities after preprocessing or 2^24 or more vertices. */
+ * game returns PG_EUNSUPPORTED only beyond that mode's limits: more than 5
+ * distinct priorities after preprocessing, or count digits (one per priority,
+ * one bit wider than the bit length of that priority's number of vertices)
+ * totalling more than 126 bits (5 priorities of 8M vertices each take 120). */
 pg_status pg_load_csr(pg_ctx *ctx, int32_t n, int64_t m, const int32_t *offsets, const int32_t *targets,
                       const uint8_t *owner, const int32_t *pri, int32_t mem_kind, pg_game **out);
 

@@ -5,9 +5,10 @@
 // Ids are ranks by (priority, input order), so the ids of one priority form
 // a range (a level) and the largest id on a cycle has the cycle's largest
 // priority. A count vector is encoded as one signed 128-bit key
-//   key(v) = sum over levels l of s_l * L_l(v) * 2^(b l),  s_l = +1 (even), -1 (odd),
-// with digits of b = L.digit_bits bits, one more than the bit length of the
-// number of ids, so every digit stays below 2^(b-1) in magnitude and keys
+//   key(v) = sum over levels l of s_l * L_l(v) * 2^(shift_l),  s_l = +1 (even), -1 (odd),
+// with the digit of level l one bit wider than the bit length of the level's
+// size (L.shift), so every digit stays below half its range in magnitude and
+// the digits below any level sum to less than that level's unit: keys
 // compare exactly as valuations do under Maxdiff: the largest level whose
 // counts differ decides, more is better when its priority is even. The key is
 // a sum of per-vertex weights along the play, computed over the same
@@ -48,7 +49,7 @@ __device__ inline i128 weight_of_counts(const Levels& L, uint64_t c) {
 #pragma unroll
     for (int l = 0; l < kMaxLevels; ++l) {
         if (l >= L.n) break;
-        const i128 d = (i128)((c >> (7 * l)) & 127u) << (L.digit_bits * l);
+        const i128 d = (i128)((c >> (7 * l)) & 127u) << L.shift[l];
         w += ((L.odd_mask >> l) & 1u) ? -d : d;
     }
     return w;
@@ -56,7 +57,7 @@ __device__ inline i128 weight_of_counts(const Levels& L, uint64_t c) {
 
 __device__ inline i128 weight_of(const Levels& L, int32_t v) {
     const int l = level_of(L, v);
-    const i128 w = (i128)1 << (L.digit_bits * l);
+    const i128 w = (i128)1 << L.shift[l];
     return ((L.odd_mask >> l) & 1u) ? -w : w;
 }
 
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(kBlock) k_switch_cv(int32_t n, int player, con
 }
 
 // Count vectors of the original vertices (rows of nlev), decoded from the
-// keys: balanced base-2^b digits (b = L.digit_bits), each the signed count of its level.
+// keys: balanced digits (level l's of width L.shift[l+1] - L.shift[l]), each the signed count of its level.
 __global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i128* __restrict__ key,
                          const uint8_t* __restrict__ cls, Levels L, int32_t* __restrict__ out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
@@ -486,7 +487,7 @@ __global__ void k_counts(int64_t n0, const int32_t* __restrict__ nid0, const i12
         i128 k = fin ? key[i] : 0;
         for (int l = 0; l < L.n; ++l) {
             // the lowest digit in (-2^(b-1), 2^(b-1)): low b bits, taken negative from 2^(b-1) up
-            const int b = L.digit_bits;
+            const int b = L.shift[l + 1] - L.shift[l];
             int64_t a = (int64_t)(k & (i128)((1ll << b) - 1));
             if (a >= (1ll << (b - 1))) a -= 1ll << b;
             k = (k - (i128)a) >> b;  // exact: k - a is a multiple of 2^b

@@ -27,11 +27,10 @@ constexpr int kJumpRoundsDeep = 4096; // extra pointer-jumping rounds allowed on
 constexpr int kHugeChildren = 4096;   // a parent with more children is ranked by an id-ordered scan instead
 constexpr int kCoopTile = 4096;       // elements per tile of the id-ordered scans
 // Count-vector mode (repeated priorities): at most kMaxLevels distinct
-// priorities; a count vector is one signed 128-bit key with one digit of
-// Levels::digit_bits bits per level, wide enough that every signed count
-// stays below half the digit's range (so the key order is the order of
-// Section 3), and levels x digit_bits <= kKeyBits (the top key stays above
-// every finite one).
+// priorities; a count vector is one signed 128-bit key with one digit per
+// level (Levels::shift), each wide enough that its signed count stays below
+// half the digit's range (so the key order is the order of Section 3), all
+// within kKeyBits bits (the top key stays above every finite one).
 constexpr int kMaxLevels = 5;
 constexpr int kKeyBits = 126;
 
@@ -180,7 +179,9 @@ struct Levels {
     int32_t n;
     uint32_t odd_mask;
     int32_t start[pg::kMaxLevels + 1];
-    int32_t digit_bits;  // bit length of the id count + 1: every count lies in (-2^(digit_bits-1), 2^(digit_bits-1))
+    int32_t shift[pg::kMaxLevels + 1];  // bit offset of level l's digit; shift[l+1] - shift[l] = its width, one bit
+                                        // more than the bit length of the level's size, so every signed count
+                                        // of level l lies in (-2^(width-1), 2^(width-1))
 };
 
 // A loaded game, or a batch of games packed into one id space. Every game's

@@ -433,17 +433,7 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
             return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities support at most 5 distinct priorities "
                                               "after preprocessing (the dummies' priority counts as one)");
         }
-        // digits: one bit more than the bit length of the ids (counts of a play never exceed them)
-        int32_t bits = 1;
-        while (bits < 40 && ((np + 1) >> bits) != 0) ++bits;
-        bits += 1;
-        if (nlev * bits > kKeyBits) {
-            free_game(g);
-            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities: levels x (bit length of the vertex "
-                                              "count + 1) must stay within 126 bits (5 priorities: fewer than 2^24 "
-                                              "vertices; 4: fewer than 2^30)");
-        }
-        g->lev.digit_bits = bits;
+
         uint8_t *lvl8, *ind;
         int32_t* pos;
         LG_TRY(T.get(&lvl8, np));
@@ -466,6 +456,23 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
             start += cnt_l;
         }
         g->lev.start[nlev] = start;
+        // digits: level l's count on a play never exceeds the level's size, so its digit takes one bit more
+        // than that size's bit length; the digits of all levels share the 126 bits below the top key
+        int32_t shift = 0;
+        for (int32_t l = 0; l < nlev; ++l) {
+            const int64_t size = (int64_t)g->lev.start[l + 1] - g->lev.start[l];
+            int32_t w = 1;
+            while (w < 40 && (size >> w) != 0) ++w;
+            g->lev.shift[l] = shift;
+            shift += w + 1;
+        }
+        g->lev.shift[nlev] = shift;
+        if (shift > kKeyBits) {
+            free_game(g);
+            return fail(ctx, PG_EUNSUPPORTED, "pg_load_csr: repeated priorities: the count digits of the levels "
+                                              "(each one bit more than the bit length of its level's size) exceed "
+                                              "126 bits");
+        }
     }
     ++ctx->launches;
     k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);

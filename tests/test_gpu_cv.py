@@ -204,16 +204,14 @@ def test_cv_limits(pg, ctx):
         assert pg.pg_game_levels(game).size == 5 and pg.pg_game_info(game)[2] == 0
     finally:
         pg.pg_game_free(game)
-    # digits of (bit length of the ids + 1) bits: 5 levels fit 126 bits below 2^24 ids, not at 2^24
+    # each level's digit is one bit wider than the bit length of the level's size: 5 levels of 2^24 / 5 ids
+    # take 5 x 23 bits, within the key's 126
     n = (1 << 24)
     off = np.arange(n + 1, dtype=np.int32)
     tgt = ((np.arange(n, dtype=np.int64) + 1) % n).astype(np.int32)
-    with pytest.raises(pg.PgError) as e:
-        pg.pg_load_csr(ctx, n, n, off, tgt, np.zeros(n, np.uint8), (np.arange(n) % 5).astype(np.int32))
-    assert e.value.code == pg.PG_EUNSUPPORTED
-    game = pg.pg_load_csr(ctx, n, n, off, tgt, np.zeros(n, np.uint8), (np.arange(n) % 4).astype(np.int32))
-    try:  # 4 levels at 2^24 ids: accepted
-        assert pg.pg_game_levels(game).size == 4
+    game = pg.pg_load_csr(ctx, n, n, off, tgt, np.zeros(n, np.uint8), (np.arange(n) % 5).astype(np.int32))
+    try:
+        assert pg.pg_game_levels(game).size == 5
     finally:
         pg.pg_game_free(game)
 

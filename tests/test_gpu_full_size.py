@@ -21,8 +21,8 @@ arrays through the C ABI, as the benchmark does (the loop as one CUDA graph).
   profile optimal (Theorem 1), so the winning regions are certified.
 
 The oracles take about half a minute per game (preprocessing, four
-valuations). A 20M-vertex game with 3 priorities (more than 2^24 ids with the
-dummies' level) checks the count-vector digits that grow with the game.
+valuations). 20M-vertex games with 3 and 4 priorities (more than 2^24 ids
+with the dummies' level) check the count-vector digits sized by level.
 """
 import hashlib
 import json
@@ -187,17 +187,13 @@ def test_full_size_count_vectors_certified(pg, ctx, game_cv):
     cert.certify_counts(gp, g.offsets, g.targets, got)
 
 
-@pytest.fixture(scope="module")
-def game_cv_big():
-    """A 20M-vertex random game with 3 priorities (4 levels with the dummies'):
-    more than 2^24 ids after preprocessing, beyond the fixed 25-bit digits."""
-    g = gen.native_random_game(20_000_000, DMIN, DMAX, 3, levels=3)
+@pytest.mark.parametrize("levels", [3, 4])
+def test_count_vectors_beyond_2_24_ids(pg, ctx, levels):
+    """20M-vertex random games with 3 and 4 priorities (4 and 5 levels with
+    the dummies'): more than 2^24 ids after preprocessing, beyond fixed 25-bit
+    digits; with 4 priorities the shape of the largest games of Table 1."""
+    g = gen.native_random_game(20_000_000, DMIN, DMAX, 3, levels=levels)
     gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
-    return g, gp
-
-
-def test_count_vectors_beyond_2_24_ids(pg, ctx, game_cv_big):
-    g, gp = game_cv_big
     assert gp["n"] + 1 > (1 << 24) and gp["k"] > 0
     rc, _, _, used, iters, got = gpu_solve(pg, ctx, g, max_inner=3)
     assert rc == pg.PG_ETIMEOUT and used and iters == 3
@@ -208,7 +204,7 @@ def test_count_vectors_beyond_2_24_ids(pg, ctx, game_cv_big):
     val = o3.valuate(gp, r["strat"])
     want = o3.map_back(gp, dict(val, strat=r["strat"]))
     assert_equal(got, want, ["win", "val_class", "val_depth", "val_counts"], "valuation")
-    assert got["val_counts"].shape == (g.n, 4)
+    assert got["val_counts"].shape == (g.n, levels + 1)
     rc, major, inner, used, iters, got = gpu_solve(pg, ctx, g)
     assert rc == pg.PG_OK and used and iters == inner and major > 0
     cert.certify_counts(gp, g.offsets, g.targets, got)
