@@ -264,7 +264,7 @@ struct pg_game {
     bool last_cmp = false;       // the last loop compared valuations: key, cls and depth are not the current ones
     // the switching player's view (built before the first loop that compares valuations): for p = 0
     // (Even, dummies included) and 1 (Odd) the ids of p's vertices in increasing order and their edge
-    // lists, contiguous (int32 offsets; not built for layouts with 64-bit offsets)
+    // lists, contiguous (int32 offsets; a player with 2^31 or more edges keeps the unsplit passes)
     bool pl_ok = false;
     int32_t* pl_vid[2] = {nullptr, nullptr};
     int32_t* pl_off[2] = {nullptr, nullptr};

@@ -41,6 +41,7 @@
 // minimiser for Odd, the sink first and then the first maximiser for Even; a
 // vertex switches only when strictly better.
 #include <cooperative_groups.h>
+#include <string.h>
 
 #include "pg_device.cuh"
 
@@ -1432,24 +1433,27 @@ __global__ void __launch_bounds__(kBlock) k_pl_mark(int32_t n, const uint8_t* __
     }
 }
 
+template <typename OffT>
 __global__ void __launch_bounds__(kBlock) k_pl_gather(int32_t n, const uint8_t* __restrict__ m,
                                                       const int32_t* __restrict__ pos,
-                                                      const int32_t* __restrict__ off, int32_t* __restrict__ vid,
+                                                      const OffT* __restrict__ off, int32_t* __restrict__ vid,
                                                       int32_t* __restrict__ deg) {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (!m[v]) continue;
         const int32_t i = pos[v];
         vid[i] = v;
-        deg[i] = off[v + 1] - off[v];
+        deg[i] = (int32_t)(off[v + 1] - off[v]);
     }
 }
 
+template <typename OffT>
 __global__ void __launch_bounds__(kBlock) k_pl_copy(int32_t np, const int32_t* __restrict__ vid,
-                                                    const int32_t* __restrict__ off, const int32_t* __restrict__ tgt,
+                                                    const OffT* __restrict__ off, const int32_t* __restrict__ tgt,
                                                     const int32_t* __restrict__ poff, int32_t* __restrict__ ptgt) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         const int32_t v = vid[i];
-        const int32_t e0 = off[v], k = off[v + 1] - e0, d0 = poff[i];
+        const OffT e0 = off[v];
+        const int32_t k = (int32_t)(off[v + 1] - e0), d0 = poff[i];
         for (int32_t j = 0; j < k; ++j) ptgt[d0 + j] = tgt[e0 + j];
     }
 }
@@ -1895,7 +1899,7 @@ pg_status full_valuation(pg_game* g, bool want_dom) {
 }
 
 pg_status build_player_split(pg_game* g) {
-    if (g->pl_ok || g->off64 || g->cv) return PG_OK;  // 64-bit layouts keep the unsplit passes
+    if (g->pl_ok || g->cv) return PG_OK;
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     const int32_t n = g->n;
@@ -1921,14 +1925,32 @@ pg_status build_player_split(pg_game* g) {
         g->pl_n[p] = np;
         PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_vid[p], sizeof(int32_t) * std::max(np, 1), s));
         PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_off[p], sizeof(int32_t) * ((size_t)np + 1), s));
-        k_pl_gather<<<grid, kBlock, 0, s>>>(n, mark[p], g->coff, g->off, g->pl_vid[p], g->hugelist);
-        PG_CUDA_TRY(ctx, exclusive_scan_i32(g->hugelist, g->pl_off[p], np, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
-        PG_CUDA_TRY(ctx, cudaMemcpyAsync(host, g->pl_off[p] + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (g->off64) k_pl_gather<int64_t><<<grid, kBlock, 0, s>>>(n, mark[p], g->coff, g->off64, g->pl_vid[p], g->hugelist);
+        else k_pl_gather<int32_t><<<grid, kBlock, 0, s>>>(n, mark[p], g->coff, g->off, g->pl_vid[p], g->hugelist);
+        // the view's offsets are 32-bit: the player's edges must number fewer than 2^31 (the scan's total is 64-bit)
+        int64_t* total = g->loop_iters;  // free before a loop
+        PG_CUDA_TRY(ctx, exclusive_scan_i32(g->hugelist, g->pl_off[p], np, total, g->scan_tmp, g->scan_tmp_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(host + 2, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        const int32_t mp = host[0];
+        int64_t mp64 = 0;
+        memcpy(&mp64, host + 2, sizeof(int64_t));
+        if (mp64 > INT32_MAX - 1) {  // too many for the view: the unsplit passes, as before any view
+            for (int q = 0; q < 2; ++q) {
+                if (g->pl_vid[q]) cudaFreeAsync(g->pl_vid[q], s);
+                if (g->pl_off[q]) cudaFreeAsync(g->pl_off[q], s);
+                if (g->pl_tgt[q]) cudaFreeAsync(g->pl_tgt[q], s);
+                g->pl_vid[q] = g->pl_off[q] = g->pl_tgt[q] = nullptr;
+            }
+            return PG_OK;
+        }
+        const int32_t mp = (int32_t)mp64;
         PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_tgt[p], sizeof(int32_t) * std::max(mp, 1), s));
-        k_pl_copy<<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_vid[p], g->off, g->tgt, g->pl_off[p],
-                                                               g->pl_tgt[p]);
+        if (g->off64)
+            k_pl_copy<int64_t><<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_vid[p], g->off64, g->tgt,
+                                                                            g->pl_off[p], g->pl_tgt[p]);
+        else
+            k_pl_copy<int32_t><<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_vid[p], g->off, g->tgt,
+                                                                            g->pl_off[p], g->pl_tgt[p]);
         PG_CUDA_TRY(ctx, cudaGetLastError());
     }
     ctx->launches += 7;
