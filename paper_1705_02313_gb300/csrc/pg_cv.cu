@@ -300,15 +300,25 @@ __global__ void __launch_bounds__(kBlock) k_jump_cv_coop(const int32_t* __restri
                 dw[v] = a;
                 continue;
             }
-            const int32_t x = gd_ptr(w);
-            const uint64_t wx = __ldcg((const unsigned long long*)(sg + x));
-            const i128 ax = sw[x];
+            int32_t x = gd_ptr(w);
+            uint64_t wx = __ldcg((const unsigned long long*)(sg + x));
+            i128 ax = sw[x];
+            i128 acc = a;
+            uint64_t pre = gd_dist(w);
+            // through up to kJumpFollow resolved vertices below v at once (their segments rise to g(x) < v)
+            for (int f = 0; f < kJumpFollow && gd_resolved(wx) && !gd_none(wx) && gd_ptr(wx) < v; ++f) {
+                acc += ax;
+                pre += gd_dist(wx);
+                x = gd_ptr(wx);
+                wx = __ldcg((const unsigned long long*)(sg + x));
+                ax = sw[x];
+            }
             uint64_t nw;
             if (gd_resolved(wx) && gd_none(wx)) {
                 nw = gd_pack(true, true, 0, gd_ptr(wx));  // v is above its whole future, in a top basin
             } else {
                 const int32_t y = gd_ptr(wx);
-                uint64_t nd = (uint64_t)gd_dist(w) + gd_dist(wx);
+                uint64_t nd = pre + gd_dist(wx);
                 if (nd > kDistMax) nd = kDistMax;
                 if (y > v) nw = gd_pack(true, false, (uint32_t)nd, y, y == sink0);
                 else if (y == v) nw = gd_pack(true, true, (uint32_t)nd, v);
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_jump_cv_coop(const int32_t* __restri
                 }
             }
             dg[v] = nw;
-            dw[v] = a + ax;
+            dw[v] = acc + ax;
             if (gd_resolved(nw)) gd32[v] = g32_word(nw);
         }
         block_add32(left, &cnt->left[r % 3]);
