@@ -148,15 +148,16 @@ def algorithmic_bytes(name, s):
     Even split of both."""
     n, m = s["n"], s["m"]
     table = {
-        "walk": 25 * n,        # strat 4 + flags 1 read; gd 8, gd32 4, size and odd-total zeros 8 written
+        "walk": 9 * n,         # compare-mode walk (the loop's): strat 4 + flags 1 read; gd32 4 written
+        "classify": 10 * n,    # gd32 4 + flags 1 read; top word 4 written; the top's parity 1 gathered
         "chain1": 15 * n,      # gd32 4 + flags 1 read; kind 1, cls 1, slot 4 written; one children-count atomic 4
         "child_scan": 8 * n,   # counts read, offsets written
         "scatter": 33 * n,     # kind 1, sz 4, gd32 4, slot 4, the parent's offset 4 read; entry 8, count 4, sink value 4 written
         "siblings": 20 * n,    # offsets 4, entries 8 read; weight 4, odd total 4 written
         "sink_scan": 8 * n,    # sink values 4 read, weights 4 written (the tile sums come with k_scatter)
         "chain2": 17 * n,      # flags 1, odd total 4, weight 4, gd32 4 read; key 4 written
-        "switch_odd": n + 12 * s["n_odd"] + 8 * s["m_odd"],
-        "switch_even": n + 16 * s["n_even"] + 8 * s["m_even"],
+        "switch_odd": 12 * s["n_odd"] + 8 * s["m_odd"],    # the Odd view: vertex, offset, strategy; target + gather
+        "switch_even": 12 * s["n_even"] + 8 * s["m_even"],
     }
     return table.get(name)
 
@@ -175,9 +176,10 @@ def kernel_entry(name, v, s, hbm):
 
 
 # where each kernel class whose DRAM traffic is recorded is defined
-KERNEL_SOURCE = {"chain1": ("pg_iter.cu", "k_chain1(")}
+KERNEL_SOURCE = {"chain1": ("pg_iter.cu", "k_chain1("), "classify": ("pg_iter.cu", "k_classify("),
+                 "walk": ("pg_iter.cu", "k_walk_cmp("), "switch_odd": ("pg_iter.cu", "k_switch_cmp_pl(")}
 # the files holding the kernels of one inner iteration (their traffic is recorded as "iteration")
-ITERATION_SOURCES = ("pg_iter.cu", "pg_scan.cu")
+ITERATION_SOURCES = ("pg_iter.cu", "pg_device.cuh", "pg_scan.cu")
 
 
 def kernel_text(path, marker):

@@ -45,7 +45,7 @@ def test_recorded_traffic_goes_stale_with_the_kernel_source(tmp_path, monkeypatc
     for d in ("paper_1705_02313_gb300/csrc", "profiles"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    rec = json.load(open(tmp_path / "profiles" / "traffic.json"))["random-10m"]["chain1"]
+    rec = json.load(open(tmp_path / "profiles" / "traffic.json"))["random-10m"]["classify"]
     rec["source_hash"] = bench.kernel_source_hash("chain1")
     json.dump({"random-10m": {"chain1": rec}}, open(tmp_path / "profiles" / "traffic.json", "w"))
     assert bench.measured_traffic("chain1", "random-10m") == rec["dram_bytes_per_launch"]
@@ -57,13 +57,14 @@ def test_recorded_traffic_goes_stale_with_the_kernel_source(tmp_path, monkeypatc
     j = text.index("{", i)
     src.write_text(text[:j + 1] + "\n    // an edit inside the kernel\n" + text[j + 1:])
     assert bench.measured_traffic("chain1", "random-10m") is None
-    assert bench.measured_traffic("walk", "random-10m") is None  # nothing recorded
+    assert bench.measured_traffic("sink_scan", "random-10m") is None  # nothing recorded
 
 
 def test_algorithmic_bytes_of_the_passes():
     s = {"n": 100, "m": 300, "n_odd": 40, "m_odd": 150, "n_even": 60, "m_even": 150}
     assert bench.algorithmic_bytes("chain1", s) == 15 * 100
-    assert bench.algorithmic_bytes("walk", s) == 25 * 100
-    assert bench.algorithmic_bytes("switch_odd", s) == 100 + 12 * 40 + 8 * 150
+    assert bench.algorithmic_bytes("walk", s) == 9 * 100
+    assert bench.algorithmic_bytes("classify", s) == 10 * 100
+    assert bench.algorithmic_bytes("switch_odd", s) == 12 * 40 + 8 * 150
     assert bench.algorithmic_bytes("sink_scan", s) == 8 * 100
     assert bench.algorithmic_bytes("no_such_kernel", s) is None
