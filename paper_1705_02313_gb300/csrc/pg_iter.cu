@@ -45,6 +45,11 @@
 
 #include "pg_device.cuh"
 
+// Vertices per thread of the loop's two chain passes (k_walk_cmp, k_classify).
+#ifndef PG_CHAIN_ILP
+#define PG_CHAIN_ILP 4
+#endif
+
 namespace cg = cooperative_groups;
 
 namespace pg {
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
 constexpr uint32_t kG32Pend = kG32None | kG32Sink;
 __device__ inline bool g32_pending(uint32_t w) { return (w & kG32Pend) == kG32Pend; }
 
-template <uint32_t cap>
+template <uint32_t cap, int ILP = kIlp>
 __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
                                                      const uint8_t* __restrict__ flags,
                                                      const int32_t* __restrict__ vgame,
@@ -203,27 +208,27 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
                                                      int32_t* more_count) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
-        int32_t v[kIlp], x[kIlp];
-        uint32_t d[kIlp];
-        bool act[kIlp], slotid[kIlp];
+        int32_t v[ILP], x[ILP];
+        uint32_t d[ILP];
+        bool act[ILP], slotid[ILP];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+        for (int j = 0; j < ILP; ++j) {
+            v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
             x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
             d[j] = 1;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < cap;
+        for (int j = 0; j < ILP; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < cap;
         for (;;) {
             bool any = false;
-            int32_t nx[kIlp];
+            int32_t nx[ILP];
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+            for (int j = 0; j < ILP; ++j) nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < ILP; ++j) {
                 if (act[j]) {
                     x[j] = nx[j];
                     ++d[j];
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
             if (!any) break;
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < ILP; ++j) {
             bool pend = false;
             if (v[j] < n) {
                 uint32_t w;
@@ -1216,20 +1221,21 @@ __device__ inline int32_t top_id(uint32_t t) { return (int32_t)(t & 0x3fffffffu)
 // in-place marks are race-free shortcuts. A cycle maximum (a none vertex whose
 // pointer is itself) with an odd priority counts toward its game's odd cycles
 // (sigma not admissible).
+template <int ILP = kIlp>
 __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags,
                                                      uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
                                                      GameState* gst, Counters* cnt, int32_t deep_cut) {
     if (cnt->err || cnt->deep) return;  // unfinished jumping: g-words may point downwards, no chain walk would end
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp_tile_base(tile) < n;
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
-        int32_t v[kIlp], x[kIlp], len[kIlp];
-        uint32_t w0[kIlp];
-        bool act[kIlp], top[kIlp];
+        int32_t v[ILP], x[ILP], len[ILP];
+        uint32_t w0[ILP];
+        bool act[ILP], top[ILP];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+        for (int j = 0; j < ILP; ++j) {
+            v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
             len[j] = 0;
             const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
             w0[j] = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
@@ -1241,11 +1247,11 @@ __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, 
         }
         for (;;) {
             bool any = false;
-            uint32_t wx[kIlp];
+            uint32_t wx[ILP];
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
+            for (int j = 0; j < ILP; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < ILP; ++j) {
                 if (act[j] && ++len[j] > deep_cut) {  // a deep forest: the iteration is abandoned (loop stops)
                     act[j] = false;
                     cnt->deep = 1;
@@ -1266,11 +1272,11 @@ __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, 
             }
             if (!any) break;
         }
-        uint8_t fx[kIlp];
+        uint8_t fx[ILP];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
+        for (int j = 0; j < ILP; ++j) fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
             if (top[j] && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
             topw[v[j]] = top[j] ? kG32Top : ((fx[j] & kPriOdd) ? kTopOdd : 0u) | (uint32_t)x[j];
@@ -1805,11 +1811,11 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
     {
-        auto walk = k_walk_cmp<kWalkCap>;
+        auto walk = k_walk_cmp<kWalkCap, PG_CHAIN_ILP>;
         switch (g->tune.walk_cap) {
-            case 16: walk = k_walk_cmp<16>; break;
-            case 32: walk = k_walk_cmp<32>; break;
-            case 128: walk = k_walk_cmp<128>; break;
+            case 16: walk = k_walk_cmp<16, PG_CHAIN_ILP>; break;
+            case 32: walk = k_walk_cmp<32, PG_CHAIN_ILP>; break;
+            case 128: walk = k_walk_cmp<128, PG_CHAIN_ILP>; break;
             default: break;
         }
         walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32, g->plist,
@@ -1828,8 +1834,8 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     }
     prof_begin(g, KID_CLASSIFY);
     // the top words live in the chain-weight array, which only a full valuation uses
-    k_classify<<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame, g->gst, c,
-                                              g->tune.deep_cut);
+    k_classify<PG_CHAIN_ILP><<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame,
+                                                            g->gst, c, g->tune.deep_cut);
     prof_end(g, KID_CLASSIFY, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
