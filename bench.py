@@ -436,6 +436,8 @@ def batch_measure(name, cpu_budget=0):
             "one_at_a_time_games_per_s": count / t_single, "speedup": t_single / t_batch,
             "batched_s": t_batch, "batched_e2e_s": t_e2e, "one_at_a_time_s": t_single,
             "lockstep_iterations": its, "inner_min": inner_lo,
+            "batched_split_ms": ({"load": res["load_ms"], "pack": res["pack_ms"], "loop": res["loop_ms"]}
+                                 if res else None),
             "inner_max": inner_hi, "valuations_one_at_a_time": inner_sum,
             "generate_s": t_gen, "identical_results": same, "cpu_baseline": cpu,
             "timing": "wall clock around each call, device synchronised; includes loading and preprocessing; "

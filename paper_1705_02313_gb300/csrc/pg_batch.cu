@@ -14,6 +14,11 @@
 
 #include "pg_internal.cuh"
 
+// Loader threads of a batch (each with its own stream).
+#ifndef PG_LOADERS
+#define PG_LOADERS 8
+#endif
+
 namespace pg {
 namespace {
 
@@ -172,7 +177,7 @@ pg_status batch_solve(pg_ctx* ctx, int32_t ngames, const int64_t* vb, const int6
     // each with its own stream, load games concurrently so that their work
     // overlaps on the device. The first failing game (in index order) decides
     // the status.
-    constexpr int kLoaders = 8;
+    constexpr int kLoaders = PG_LOADERS;
     const int nload = std::max(1, std::min<int>(kLoaders, ngames));
     std::vector<pg_ctx*> lctx(nload, nullptr);
     std::vector<pg_status> gst_load(ngames, PG_OK);

@@ -199,17 +199,29 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
 constexpr uint32_t kG32Pend = kG32None | kG32Sink;
 __device__ inline bool g32_pending(uint32_t w) { return (w & kG32Pend) == kG32Pend; }
 
+// Packed games: a warp tile of consecutive ids inside one game that is no
+// longer active is skipped by the loop's chain passes (its words are not read
+// by any active game: plays stay inside their game, and the full valuation
+// after the loop recomputes every game). Warp-uniform.
+__device__ inline bool tile_idle(int64_t t0, int64_t t1, int32_t n, const int32_t* __restrict__ vgame,
+                                 const GameState* __restrict__ gst) {
+    if (!vgame) return false;
+    const int32_t a = vgame[t0], b = vgame[(int32_t)(t1 < n ? t1 : n) - 1];
+    return a == b && gst[a].phase != kPhaseActive;
+}
+
 template <uint32_t cap, int ILP = kIlp>
 __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
                                                      const uint8_t* __restrict__ flags,
                                                      const int32_t* __restrict__ vgame,
                                                      const int32_t* __restrict__ gsink, int32_t sink0,
                                                      uint32_t* __restrict__ gd32, int32_t* __restrict__ more,
-                                                     int32_t* more_count) {
+                                                     int32_t* more_count, const GameState* __restrict__ gst) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
+        if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP];
         uint32_t d[ILP];
         bool act[ILP], slotid[ILP];
@@ -1230,6 +1242,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, 
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
+        if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP], len[ILP];
         uint32_t w0[ILP];
         bool act[ILP], top[ILP];
@@ -1819,7 +1832,7 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
             default: break;
         }
         walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32, g->plist,
-                                            &c->n_pending);
+                                            &c->n_pending, g->gst);
     }
     prof_end(g, KID_WALK, 1);
     {
