@@ -91,7 +91,7 @@ void free_game(pg_game* g) {
                     g->tiles, g->tsum,   g->cnt,    g->scan_tmp, g->stage, g->loop_iters, g->ws, g->wsB, g->gdB, g->key128,
                     g->d_anc, g->d_sc, g->d_podd, g->d_peven, g->d_oddL, g->d_evenL, g->d_nxt, g->d_wt, g->d_loc,
                     g->d_own, g->d_rid, g->d_rl, g->d_val, g->d_rnx, g->pl_vid[0], g->pl_vid[1], g->pl_off[0],
-                    g->pl_off[1], g->pl_tgt[0], g->pl_tgt[1]};
+                    g->pl_off[1], g->pl_tgt[0], g->pl_tgt[1], g->rv_off, g->rv_src, g->omark};
     int prev = -1;
     const bool switched =
         cudaGetDevice(&prev) == cudaSuccess && prev != g->device && cudaSetDevice(g->device) == cudaSuccess;
@@ -486,6 +486,8 @@ pg_status run_loop(pg_game* g, int64_t cap, bool even, Timer& tm, int64_t limit)
         pg_status st = build_player_split(g);
         if (st) return st;
     }
+    if (omark_of(g))  // the first Odd pass of the call evaluates every Odd vertex (a nonzero flag)
+        PG_CUDA_TRY(g->ctx, cudaMemsetAsync(g->gactive + 1, 0xff, sizeof(int32_t), g->ctx->stream));
     int64_t done = 0;
     for (;;) {
         int64_t ran = 0;

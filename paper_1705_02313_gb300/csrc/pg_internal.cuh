@@ -270,6 +270,13 @@ struct pg_game {
     int32_t* pl_off[2] = {nullptr, nullptr};
     int32_t* pl_tgt[2] = {nullptr, nullptr};
     int64_t pl_n[2] = {0, 0};
+    // built with the views: Odd's reverse view (for every id t, rv_src[rv_off[t] .. rv_off[t+1]) are the
+    // positions in Odd's view of the vertices with an edge to t) and omark (one byte per position of Odd's
+    // view, zero padded to a multiple of 16): the vertices that the next Odd switching pass evaluates unless
+    // it is full; the others keep their decision (see k_classify)
+    int32_t* rv_off = nullptr;
+    int32_t* rv_src = nullptr;
+    uint8_t* omark = nullptr;
     // ruling-set ranks (pg_deep.cu), for games whose g-forest is deep
     bool deep_mode = false;      // every valuation of the current call takes the ruling-set path
     bool val_deep = false;       // the last valuation took it (its depths are written; no depth pass)
@@ -384,6 +391,7 @@ pg_status enqueue_switch(pg_game* g, int player);
 // The loop's iterations without ranks: the nearest-greater forest and the class of every vertex, then
 // switching passes that compare the valuations of two successors by walking their g-chains.
 bool loop_compares(const pg_game* g);
+uint8_t* omark_of(const pg_game* g);  // the Odd marks in use by the loop, or null
 pg_status enqueue_valuation_cmp(pg_game* g);
 pg_status enqueue_switch_cmp(pg_game* g, int player);
 // After a loop that compared valuations: the full valuation of the current profile (key, cls, depth).

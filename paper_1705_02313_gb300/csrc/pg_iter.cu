@@ -1172,6 +1172,7 @@ __global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even
                 else {
                     st.major += 1;
                     st.reset = reset_mode;
+                    if (reset_mode) atomicOr(gactive + 1, 1);  // Odd restarts: the next Odd pass is full
                 }
             }
             if (st.phase == kPhaseActive && st.inner >= cap) st.phase = kPhaseTimeout;
@@ -1184,7 +1185,8 @@ __global__ void k_bookkeep(int32_t ngames, GameState* gst, int64_t cap, int even
 }
 
 // SI-Reset (Section 6): in games marked by k_bookkeep, every Odd vertex goes
-// back to the first edge of its list (the initial strategy of Algorithm 1).
+// back to the first edge of its list (the initial strategy of Algorithm 1);
+// k_bookkeep has set the flag that makes the next Odd switching pass full.
 template <typename OffT>
 __global__ void __launch_bounds__(kBlock) k_reset_odd(int32_t n, const OffT* __restrict__ off,
                                                       const int32_t* __restrict__ tgt,
@@ -1233,18 +1235,31 @@ __device__ inline int32_t top_id(uint32_t t) { return (int32_t)(t & 0x3fffffffu)
 // in-place marks are race-free shortcuts. A cycle maximum (a none vertex whose
 // pointer is itself) with an odd priority counts toward its game's odd cycles
 // (sigma not admissible).
+//
+// With omark, a top word is written only when it differs from the previous
+// iteration's, and then every Odd vertex with an edge to v (rv_off, rv_src)
+// is marked for the next Odd switching pass. An Odd vertex decides from its
+// successors' top words alone, unless two finite successors with the best
+// top tie (a chain comparison, which leaves its mark set): so an unmarked
+// vertex, none of whose successors changed since it was last evaluated,
+// would take the same decision again and is skipped. Before a full Odd pass
+// (*full != 0) no marks are needed. Eight blocks per SM: the pass is bound
+// by the latency of its chain gathers.
 template <int ILP = kIlp>
-__global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags,
-                                                     uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
-                                                     GameState* gst, Counters* cnt, int32_t deep_cut) {
+__global__ void __launch_bounds__(kBlock, 2048 / kBlock)
+    k_classify(int32_t n, uint32_t* gd32, const uint8_t* __restrict__ flags, uint32_t* __restrict__ topw,
+               const int32_t* __restrict__ vgame, GameState* gst, Counters* cnt, int32_t deep_cut,
+               const int32_t* __restrict__ rv_off, const int32_t* __restrict__ rv_src, uint8_t* omark,
+               const int32_t* __restrict__ full) {
     if (cnt->err || cnt->deep) return;  // unfinished jumping: g-words may point downwards, no chain walk would end
+    if (omark && *full) omark = nullptr;  // the next Odd pass evaluates every Odd vertex: no marks
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
         if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP], len[ILP];
-        uint32_t w0[ILP];
+        uint32_t w0[ILP], ot[ILP];
         bool act[ILP], top[ILP];
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
@@ -1287,12 +1302,22 @@ __global__ void __launch_bounds__(kBlock) k_classify(int32_t n, uint32_t* gd32, 
         }
         uint8_t fx[ILP];
 #pragma unroll
-        for (int j = 0; j < ILP; ++j) fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
+        for (int j = 0; j < ILP; ++j) {
+            fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
+            ot[j] = (omark && v[j] < n) ? topw[v[j]] : 0u;
+        }
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
             if (top[j] && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
-            topw[v[j]] = top[j] ? kG32Top : ((fx[j] & kPriOdd) ? kTopOdd : 0u) | (uint32_t)x[j];
+            const uint32_t tw = top[j] ? kG32Top : ((fx[j] & kPriOdd) ? kTopOdd : 0u) | (uint32_t)x[j];
+            if (!omark) {
+                topw[v[j]] = tw;
+            } else if (tw != ot[j]) {
+                topw[v[j]] = tw;
+                const int32_t e1 = rv_off[v[j] + 1];
+                for (int32_t e = rv_off[v[j]]; e < e1; ++e) omark[rv_src[e]] = 1;
+            }
         }
     }
 }
@@ -1477,9 +1502,103 @@ __global__ void __launch_bounds__(kBlock) k_pl_copy(int32_t np, const int32_t* _
     }
 }
 
+// Odd's reverse view: the in-degree of every id from Odd's edges, then each
+// edge's source (its position in Odd's view) at the next free slot of its
+// target (the order within a list is arbitrary; the lists only mark).
+__global__ void __launch_bounds__(kBlock) k_rv_count(int32_t np, const int32_t* __restrict__ poff,
+                                                     const int32_t* __restrict__ ptgt, int32_t* __restrict__ cnt) {
+    const int32_t m = poff[np];
+    for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x)
+        atomicAdd(cnt + ptgt[e], 1);
+}
+
+__global__ void __launch_bounds__(kBlock) k_rv_fill(int32_t np, const int32_t* __restrict__ poff,
+                                                    const int32_t* __restrict__ ptgt,
+                                                    const int32_t* __restrict__ rv_off, int32_t* __restrict__ cur,
+                                                    int32_t* __restrict__ rv_src) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        for (int32_t e = poff[i]; e < poff[i + 1]; ++e) {
+            const int32_t t = ptgt[e];
+            rv_src[rv_off[t] + atomicAdd(cur + t, 1)] = i;
+        }
+    }
+}
+
+// One vertex of k_switch_cmp_pl: view position i (vertex vid[i]), with the
+// rules of k_switch_cmp. Returns whether it switched; *tie tells whether the
+// decision took a chain comparison (two finite successors with the best top
+// so far), *gi is its game. Vertices of games that do not switch this player
+// now are left alone (tie set, no switch).
+__device__ inline bool switch_at(int32_t i, int player, const int32_t* __restrict__ vid,
+                                 const int32_t* __restrict__ poff, const int32_t* __restrict__ ptgt,
+                                 const uint8_t* __restrict__ flags, const uint32_t* __restrict__ gd32,
+                                 const uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
+                                 const int32_t* __restrict__ gsink, int32_t sink0, const GameState* gst,
+                                 int32_t* strat, bool* tie_out, int32_t* gi_out) {
+    const int32_t v = vid[i];
+    const int32_t gi = vgame ? vgame[v] : 0;
+    *gi_out = gi;
+    *tie_out = true;
+    if (vgame) {
+        const GameState st = gst[gi];
+        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return false;
+    }
+    const int32_t e0 = poff[i], e1 = poff[i + 1];
+    const int32_t cur = strat[v];
+    const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : -1;
+    int32_t best = sk;  // Even: the sink first; Odd: none yet
+    uint32_t tbest = 0;
+    bool cur_top = false, tie = false;
+    for (int32_t e = e0; e < e1; e += 4) {
+        int32_t t[4];
+        uint32_t tt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? ptgt[e + j] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tt[j] = t[j] >= 0 ? topw[t[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (t[j] < 0) continue;
+            if (t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
+            bool take;
+            if (player == 1) {
+                tie |= best >= 0 && !((tt[j] | tbest) & kG32Top) && top_id(tt[j]) == top_id(tbest);
+                take = best < 0 || cmp_val(t[j], tt[j], best, tbest, gd32, flags) < 0;
+            } else take = (best == sk ? cmp_sink(tt[j]) : cmp_val(t[j], tt[j], best, tbest, gd32, flags)) > 0;
+            if (take) {
+                best = t[j];
+                tbest = tt[j];
+            }
+        }
+    }
+    *tie_out = tie;
+    const bool sw = best != cur && (player == 0 ? !cur_top : !(tbest & kG32Top));
+    if (sw) strat[v] = best;
+    return sw;
+}
+
+// A switch counted into its game (packed games: one atomic per group of
+// lanes of the same game; one game: the block total at the end).
+__device__ inline void count_switch(bool sw, int32_t gi, int player, const int32_t* vgame, GameState* gst,
+                                    int32_t* nsw) {
+    if (!sw) return;
+    ++*nsw;
+    if (vgame) {
+        cg::coalesced_group swg = cg::coalesced_threads();
+        cg::coalesced_group same = cg::labeled_partition(swg, gi);
+        if (same.thread_rank() == 0) atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+    }
+}
+
 // k_switch_cmp over a player's view: thread i takes the player's i-th vertex.
-template <int BS>
-__global__ void __launch_bounds__(BS) k_switch_cmp_pl(int32_t np, int player, const int32_t* __restrict__ vid,
+// With MARKS (Odd's pass; omark holds one byte per view position, zero padded
+// to a multiple of 16), a pass that is not full evaluates only the marked
+// positions and clears the mark of each unless its decision took a chain
+// comparison; a full pass (the first of a call, or after an SI-Reset:
+// *full_flag != 0) evaluates every vertex and sets each mark to that flag.
+// Full occupancy (32 registers): the evaluations wait on their gathers.
+template <int BS, bool MARKS>
+__global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int player, const int32_t* __restrict__ vid,
                                                       const int32_t* __restrict__ poff,
                                                       const int32_t* __restrict__ ptgt,
                                                       const uint8_t* __restrict__ flags,
@@ -1487,56 +1606,62 @@ __global__ void __launch_bounds__(BS) k_switch_cmp_pl(int32_t np, int player, co
                                                       const uint32_t* __restrict__ topw,
                                                       const int32_t* __restrict__ vgame,
                                                       const int32_t* __restrict__ gsink, int32_t sink0,
-                                                      GameState* gst, int32_t* strat, Counters* cnt) {
+                                                      GameState* gst, int32_t* strat, Counters* cnt,
+                                                      uint8_t* omark, const int32_t* __restrict__ full_flag) {
     if (cnt->err || cnt->deep) return;  // unfinished jumping, or a deep forest (the loop stops)
     if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
         const GameState st = gst[0];
         if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
     }
+    const bool full = !MARKS || *full_flag;
     int32_t nsw = 0;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-        const int32_t v = vid[i];
-        const int32_t gi = vgame ? vgame[v] : 0;
-        if (vgame) {
-            const GameState st = gst[gi];
-            if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) continue;
+    if (full) {
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+            bool tie;
+            int32_t gi;
+            const bool sw = switch_at(i, player, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0, gst, strat,
+                                      &tie, &gi);
+            if (MARKS) omark[i] = tie;
+            count_switch(sw, gi, player, vgame, gst, &nsw);
         }
-        const int32_t e0 = poff[i], e1 = poff[i + 1];
-        const int32_t cur = strat[v];
-        const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : -1;
-        int32_t best = sk;  // Even: the sink first; Odd: none yet
-        uint32_t tbest = 0;
-        bool cur_top = false;
-        for (int32_t e = e0; e < e1; e += 4) {
-            int32_t t[4];
-            uint32_t tt[4];
+    } else if (MARKS) {
+        // warps take 512 positions at a time: each lane loads 16 marks, the marked positions are listed in
+        // shared memory (a warp scan of the lanes' counts), and the lanes share the list, so a chunk costs
+        // one 16-byte load per lane plus ceil(marked / 32) evaluation rounds
+        __shared__ int32_t list[BS / 32][512];
+        int32_t* mine = list[threadIdx.x >> 5];
+        const int lane = threadIdx.x & 31;
+        const int32_t nch = (np + 511) >> 9;
+        const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
+        for (int32_t c = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < nch; c += nw) {
+            const int32_t q = (c << 9) + 16 * lane;
+            uint4 m = make_uint4(0u, 0u, 0u, 0u);
+            if (q < np) m = *reinterpret_cast<const uint4*>(omark + q);
+            const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+            const int k = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);  // marks are 0 or 1
+            int incl = k;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) t[j] = e + j < e1 ? ptgt[e + j] : -1;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) tt[j] = t[j] >= 0 ? topw[t[j]] : 0u;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (t[j] < 0) continue;
-                if (t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
-                bool take;
-                if (player == 1) take = best < 0 || cmp_val(t[j], tt[j], best, tbest, gd32, flags) < 0;
-                else take = (best == sk ? cmp_sink(tt[j]) : cmp_val(t[j], tt[j], best, tbest, gd32, flags)) > 0;
-                if (take) {
-                    best = t[j];
-                    tbest = tt[j];
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
             }
-        }
-        const bool sw = best != cur && (player == 0 ? !cur_top : !(tbest & kG32Top));
-        if (sw) {
-            strat[v] = best;
-            ++nsw;
-            if (vgame) {  // one count per group of lanes of the same game
-                cg::coalesced_group swg = cg::coalesced_threads();
-                cg::coalesced_group same = cg::labeled_partition(swg, gi);
-                if (same.thread_rank() == 0)
-                    atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) continue;  // no successor of these 512 changed its top word
+            int pos = incl - k;
+#pragma unroll
+            for (int b = 0; b < 16; ++b)
+                if ((mw[b >> 2] >> (8 * (b & 3))) & 1u) mine[pos++] = q + b;
+            __syncwarp();
+            for (int j = lane; j < total; j += 32) {
+                const int32_t i = mine[j];  // < np: the padding is never marked
+                bool tie;
+                int32_t gi;
+                const bool sw = switch_at(i, player, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0, gst,
+                                          strat, &tie, &gi);
+                if (!tie) omark[i] = 0;
+                count_switch(sw, gi, player, vgame, gst, &nsw);
             }
+            __syncwarp();
         }
     }
     block_add(nsw, &cnt->n_switch);
@@ -1610,7 +1735,7 @@ pg_status alloc_scratch(pg_game* g) {
     PG_CUDA_TRY(ctx, A((void**)&g->tsum, sizeof(int64_t) * (2 * g->ntiles + 2)));
     PG_CUDA_TRY(ctx, A((void**)&g->gscan, sizeof(int64_t) * 3 * (size_t)g->ngames));
     PG_CUDA_TRY(ctx, A((void**)&g->gst, sizeof(GameState) * (size_t)g->ngames));
-    PG_CUDA_TRY(ctx, A((void**)&g->gactive, sizeof(int32_t)));
+    PG_CUDA_TRY(ctx, A((void**)&g->gactive, 2 * sizeof(int32_t)));
     PG_CUDA_TRY(ctx, A((void**)&g->loop_iters, sizeof(int64_t)));
     PG_CUDA_TRY(ctx, A((void**)&g->cnt, sizeof(Counters)));
     PG_CUDA_TRY(ctx, cudaMallocHost((void**)&g->hcnt, sizeof(Counters)));
@@ -1791,13 +1916,19 @@ pg_status enqueue_switch(pg_game* g, int player) {
 pg_status enqueue_bookkeeping(pg_game* g, int64_t cap, bool even_phase) {
     pg_ctx* ctx = g->ctx;
     cudaStream_t s = ctx->stream;
-    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gactive, 0, sizeof(int32_t), s));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(g->gactive, 0, 2 * sizeof(int32_t), s));
     ctx->launches += 1;
     const unsigned b = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->ngames + kBlock - 1) / kBlock, 1024));
     k_bookkeep<<<b, kBlock, 0, s>>>(g->ngames, g->gst, cap, even_phase ? 1 : 0, g->reset_tau ? 1 : 0, g->gactive,
                                     g->cnt);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
+}
+
+// The Odd marks when the loop compares valuations over the players' views
+// (null otherwise: every Odd vertex is evaluated in every pass).
+uint8_t* omark_of(const pg_game* g) {
+    return g->pl_ok && g->omark && !g->cv && !g->tune.loop_ranks && !g->deep_mode ? g->omark : nullptr;
 }
 
 pg_status enqueue_reset(pg_game* g) {
@@ -1848,7 +1979,8 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     prof_begin(g, KID_CLASSIFY);
     // the top words live in the chain-weight array, which only a full valuation uses
     k_classify<PG_CHAIN_ILP><<<ilp_grid(n), kBlock, 0, s>>>(n, g->gd32, g->flags, (uint32_t*)g->wgt, g->vgame,
-                                                            g->gst, c, g->tune.deep_cut);
+                                                            g->gst, c, g->tune.deep_cut, g->rv_off, g->rv_src,
+                                                            omark_of(g), g->gactive + 1);
     prof_end(g, KID_CLASSIFY, 1);
     PG_CUDA_TRY(ctx, cudaGetLastError());
     return PG_OK;
@@ -1867,9 +1999,11 @@ void launch_switch_cmp_bs(pg_game* g, int player) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int64_t wave = (int64_t)std::max(sms, 1) * (2048 / BS);
         const int64_t b = std::max<int64_t>(1, std::min<int64_t>((np + BS - 1) / BS, wave));
-        k_switch_cmp_pl<BS><<<(unsigned)b, BS, 0, s>>>((int32_t)np, player, g->pl_vid[player], g->pl_off[player],
-                                                       g->pl_tgt[player], g->flags, g->gd32, topw, g->vgame, g->gsink,
-                                                       g->sink0, g->gst, g->strat, g->cnt);
+        uint8_t* om = player == 1 ? omark_of(g) : nullptr;
+        auto kern = om ? k_switch_cmp_pl<BS, true> : k_switch_cmp_pl<BS, false>;
+        kern<<<(unsigned)b, BS, 0, s>>>((int32_t)np, player, g->pl_vid[player], g->pl_off[player], g->pl_tgt[player],
+                                        g->flags, g->gd32, topw, g->vgame, g->gsink, g->sink0, g->gst, g->strat,
+                                        g->cnt, om, g->gactive + 1);
         return;
     }
     const int64_t b = std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + BS - 1) / BS, 152LL * 64 * kBlock / BS));
@@ -1930,6 +2064,11 @@ pg_status build_player_split(pg_game* g) {
         if (g->pl_tgt[p]) cudaFreeAsync(g->pl_tgt[p], s);
         g->pl_vid[p] = g->pl_off[p] = g->pl_tgt[p] = nullptr;
     }
+    for (void** q : {(void**)&g->rv_off, (void**)&g->rv_src, (void**)&g->omark}) {
+        if (*q) cudaFreeAsync(*q, s);
+        *q = nullptr;
+    }
+    int32_t mp_of[2] = {0, 0};
     // the valuation's scratch is free before a loop: marks in kind and cls, positions in coff, degrees in
     // hugelist
     uint8_t* mark[2] = {g->kind, g->cls};
@@ -1963,6 +2102,7 @@ pg_status build_player_split(pg_game* g) {
             return PG_OK;
         }
         const int32_t mp = (int32_t)mp64;
+        mp_of[p] = mp;
         PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->pl_tgt[p], sizeof(int32_t) * std::max(mp, 1), s));
         if (g->off64)
             k_pl_copy<int64_t><<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_vid[p], g->off64, g->tgt,
@@ -1973,6 +2113,23 @@ pg_status build_player_split(pg_game* g) {
         PG_CUDA_TRY(ctx, cudaGetLastError());
     }
     ctx->launches += 7;
+    {  // Odd's reverse view, counted in hugelist (free again)
+        const int32_t np = (int32_t)g->pl_n[1];
+        int32_t* cnt = g->hugelist;
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->rv_off, sizeof(int32_t) * ((size_t)n + 1), s));
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->rv_src, sizeof(int32_t) * std::max(mp_of[1], 1), s));
+        const size_t mark_bytes = ((size_t)np + 16) & ~(size_t)15;  // read 16 at a time, the padding zero
+        PG_CUDA_TRY(ctx, dev_alloc(ctx, (void**)&g->omark, mark_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(g->omark, 0, mark_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s));
+        k_rv_count<<<grid_for(std::max(mp_of[1], 1)), kBlock, 0, s>>>(np, g->pl_off[1], g->pl_tgt[1], cnt);
+        PG_CUDA_TRY(ctx, exclusive_scan_i32(cnt, g->rv_off, n, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
+        PG_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s));
+        k_rv_fill<<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_off[1], g->pl_tgt[1], g->rv_off, cnt,
+                                                               g->rv_src);
+        PG_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->launches += 5;
+    }
     g->pl_ok = true;
     return PG_OK;
 }
