@@ -195,9 +195,13 @@ __global__ void __launch_bounds__(kBlock) k_jump_coop(const int32_t* __restrict_
 // Compare-mode K1 (loop iterations that compare valuations): the same walks
 // and jumps with 4-byte g-words only. A word with both the none and the sink
 // bit set is pending: its low bits are a jump pointer (every vertex strictly
-// between v and it on the play is below v, and so is the pointer).
+// between v and it on the play is below v, and so is the pointer). A word
+// with only the sink bit (g(v) is the game's sink slot, which the word does
+// not repeat) carries v's priority parity in bit 0, so that the vertex that
+// ends a chain gives its top's parity with no further read.
 constexpr uint32_t kG32Pend = kG32None | kG32Sink;
 __device__ inline bool g32_pending(uint32_t w) { return (w & kG32Pend) == kG32Pend; }
+__device__ inline uint32_t g32_sink_word(uint8_t fl) { return kG32Sink | ((fl & kPriOdd) ? 1u : 0u); }
 
 // Packed games: a warp tile of consecutive ids inside one game that is no
 // longer active is skipped by the loop's chain passes (its words are not read
@@ -211,7 +215,7 @@ __device__ inline bool tile_idle(int64_t t0, int64_t t1, int32_t n, const int32_
 }
 
 template <uint32_t cap, int ILP = kIlp>
-__global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
+__global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
                                                      const uint8_t* __restrict__ flags,
                                                      const int32_t* __restrict__ vgame,
                                                      const int32_t* __restrict__ gsink, int32_t sink0,
@@ -223,17 +227,18 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
          tile += nwarps) {
         if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP];
-        uint32_t d[ILP];
+        uint32_t d[ILP];  // steps; bit 16: v's priority is odd
         bool act[ILP], slotid[ILP];
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
-            slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
+            const uint8_t fv = v[j] < n ? flags[v[j]] : 0;
+            slotid[j] = (fv & kSinkSlot) != 0;
             x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
-            d[j] = 1;
+            d[j] = 1u | ((fv & kPriOdd) ? 0x10000u : 0u);
         }
 #pragma unroll
-        for (int j = 0; j < ILP; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && d[j] < cap;
+        for (int j = 0; j < ILP; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && (d[j] & 0xffffu) < cap;
         for (;;) {
             bool any = false;
             int32_t nx[ILP];
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
                 if (act[j]) {
                     x[j] = nx[j];
                     ++d[j];
-                    act[j] = x[j] < v[j] && d[j] < cap;
+                    act[j] = x[j] < v[j] && (d[j] & 0xffffu) < cap;
                 }
                 any |= act[j];
             }
@@ -255,8 +260,9 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
             bool pend = false;
             if (v[j] < n) {
                 uint32_t w;
-                if (slotid[j]) w = kG32Sink | (uint32_t)v[j];  // a sink slot: inert
-                else if (x[j] > v[j]) w = (x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink : 0u) | (uint32_t)x[j];
+                if (slotid[j]) w = kG32Sink;  // a sink slot: inert (its own top, even)
+                else if (x[j] > v[j])
+                    w = x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink | (d[j] >> 16) : (uint32_t)x[j];
                 else if (x[j] == v[j]) w = kG32None | (uint32_t)v[j];  // v is its cycle's maximum
                 else {
                     w = kG32Pend | (uint32_t)x[j];
@@ -273,6 +279,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_cmp(int32_t n, const int32_t* _
 // Pointer jumping on the 4-byte words for the walks that ran out of steps,
 // all rounds in one cooperative launch (as k_jump_coop, without walk lengths).
 __global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restrict__ plist, uint32_t* gd32,
+                                                        const uint8_t* __restrict__ flags,
                                                         const int32_t* __restrict__ vgame,
                                                         const int32_t* __restrict__ gsink, int32_t sink0,
                                                         Counters* cnt, int32_t cap, int cap_deep) {
@@ -296,8 +303,9 @@ __global__ void __launch_bounds__(kBlock) k_jump32_coop(const int32_t* __restric
                 // x is above its whole future and below v: so is v (same cycle)
                 nw = kG32None | (uint32_t)g32_ptr(wx);
             } else {
-                const int32_t y = g32_ptr(wx);
-                if (y > v) nw = (y == sink_of(v, vgame, gsink, sink0) ? kG32Sink : 0u) | (uint32_t)y;
+                const int32_t sk = sink_of(v, vgame, gsink, sink0);
+                const int32_t y = (g32_sink(wx) && !g32_pending(wx)) ? sk : g32_ptr(wx);
+                if (y > v) nw = y == sk ? g32_sink_word(flags[v]) : (uint32_t)y;
                 else if (y == v) nw = kG32None | (uint32_t)v;
                 else {
                     nw = kG32Pend | (uint32_t)y;
@@ -1270,6 +1278,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
             top[j] = g32_none(w0[j]);
             x[j] = g32_sink(w0[j]) ? v[j] : g32_ptr(w0[j]);  // a child of the sink is its own top
             act[j] = !(w0[j] & (kG32None | kG32Sink));
+            if (g32_sink(w0[j])) len[j] = (int32_t)((w0[j] & 1u) << 30);  // once a chain ends: its top's parity
             if (v[j] < n && g32_none(w0[j]) && x[j] == v[j] && (flags[v[j]] & kPriOdd))
                 atomicAdd(&gst[vgame ? vgame[v[j]] : 0].nodd, 1);
         }
@@ -1289,6 +1298,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
                         top[j] = true;
                         act[j] = false;
                     } else if (g32_sink(wx[j])) {  // x is the top
+                        len[j] = (int32_t)((wx[j] & 1u) << 30);
                         act[j] = false;
                     } else {
                         const int32_t nx = g32_ptr(wx[j]);
@@ -1300,17 +1310,13 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
             }
             if (!any) break;
         }
-        uint8_t fx[ILP];
 #pragma unroll
-        for (int j = 0; j < ILP; ++j) {
-            fx[j] = (v[j] < n && !top[j]) ? flags[x[j]] : 0;
-            ot[j] = (omark && v[j] < n) ? topw[v[j]] : 0u;
-        }
+        for (int j = 0; j < ILP; ++j) ot[j] = (omark && v[j] < n) ? topw[v[j]] : 0u;
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
             if (top[j] && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
-            const uint32_t tw = top[j] ? kG32Top : ((fx[j] & kPriOdd) ? kTopOdd : 0u) | (uint32_t)x[j];
+            const uint32_t tw = top[j] ? kG32Top : ((len[j] >> 30) & 1 ? kTopOdd : 0u) | (uint32_t)x[j];
             if (!omark) {
                 topw[v[j]] = tw;
             } else if (tw != ot[j]) {
@@ -1970,7 +1976,7 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
         int32_t cap = 64;
         for (int64_t x = n; x > 1; x >>= 1) cap += 2;
         int cap_deep = ctx->deep_fallback ? 1 : 0;
-        void* args[] = {(void*)&g->plist, (void*)&g->gd32, (void*)&g->vgame, (void*)&g->gsink,
+        void* args[] = {(void*)&g->plist, (void*)&g->gd32, (void*)&g->flags, (void*)&g->vgame, (void*)&g->gsink,
                         (void*)&g->sink0, (void*)&c,       (void*)&cap,      (void*)&cap_deep};
         prof_begin(g, KID_JUMP);
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_jump32_coop, g->coop_blocks, kBlock, args, 0, s));
