@@ -366,12 +366,12 @@ pg_status pg_best_response_bf(pg_game *game, const int32_t *sigma, const int8_t 
  * successor outside [0, n] (outputs are then unspecified), PG_ECUDA for a CUDA
  * error. No message is recorded.
  *
- * Set-up: the first call on a device (with that device current) looks up the
- * fixed array's device address and the cooperative launch size and keeps them
- * for the life of the process (so a cudaDeviceReset on that device must not be
- * followed by further calls). All calls share the array and it keeps the last
- * call's contents (each call clears what must start at zero), so calls that
- * overlap on the GPU, from any thread or stream, race: serialise them. */
+ * Set-up: every call looks up the fixed array's device address on the current
+ * device (a lookup, no allocation); the first call on a device also computes
+ * the cooperative launch size and keeps it. All calls share the array and it
+ * keeps the last call's contents (each call clears what must start at zero),
+ * so calls that overlap on the GPU, from any thread or stream, race:
+ * serialise them. */
 pg_status pg_valuate_static(int32_t n, const int32_t *succ, const uint8_t *odd, int8_t *val_class,
                             int32_t *val_depth, int32_t *val_rank, void *stream);
 

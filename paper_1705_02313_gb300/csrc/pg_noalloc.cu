@@ -4,8 +4,9 @@
 //
 // The working memory is one file-scope device array of kStaticBytes bytes,
 // sized for kStaticMaxN vertices. Host code cannot use the array's name as a
-// device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it. The call
+// device address, so every call looks the address up with
+// cudaGetSymbolAddress (with the call's device current; the lookup allocates
+// nothing, and a context made after a device reset gets the new address). The call
 // then lays out the valuation's arrays inside the static buffer, copies the
 // successor function into it (a successor outside [0, n] is recorded and
 // replaced by the sink, so no kernel reads out of bounds), runs the same
@@ -72,7 +73,6 @@ constexpr size_t kStaticBytes = kLayout.bytes;
 // Every call shares this buffer; it keeps the last call's contents.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-unsigned char* g_static_addr[kMaxDevices] = {};
 int g_static_coop[kMaxDevices] = {};
 int g_static_chain1[kMaxDevices] = {};
 std::mutex g_static_mu;
@@ -114,21 +114,22 @@ __global__ void k_static_results(int32_t n, const uint8_t* __restrict__ cls, con
     }
 }
 
-// Device address of the static buffer on the current device (first call per device).
+// Device address of the static buffer on the current device (looked up on
+// every call), and the launch sizes (computed once per device: they depend on
+// the device's SM count and the kernels' resources only).
 pg_status static_setup(pg_ctx* ctx, unsigned char** base, int* coop, int* chain1) {
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return PG_EUNSUPPORTED;
-    if (!g_static_addr[ctx->device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) return PG_ECUDA;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) return PG_ECUDA;
+    if (!g_static_coop[ctx->device]) {
         int cb = 0, c1 = 0;
         if (coop_blocks_for(ctx, &cb) != PG_OK || chain1_blocks_for(ctx, &c1) != PG_OK) return PG_ECUDA;
-        g_static_coop[ctx->device] = cb;
         g_static_chain1[ctx->device] = c1;
-        g_static_addr[ctx->device] = (unsigned char*)p;
+        g_static_coop[ctx->device] = cb;
     }
-    *base = g_static_addr[ctx->device];
+    *base = (unsigned char*)p;
     *coop = g_static_coop[ctx->device];
     *chain1 = g_static_chain1[ctx->device];
     return PG_OK;
