@@ -193,8 +193,15 @@ __global__ void k_relabel_degree(int32_t np, int32_t n0, const int32_t* off, con
     }
 }
 
+// New id of each input vertex as the target of an edge from U: its dummy's for
+// a vertex of W (the edge is redirected to the dummy), its own otherwise.
+__global__ void k_nid_u(int32_t n0, const uint8_t* isW, const int32_t* widx, const int32_t* nid, int32_t* nidu) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
+        nidu[v] = isW[v] ? nid[n0 + widx[v]] : nid[v];
+}
+
 __global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int32_t* off, const int32_t* tgt,
-                               const uint8_t* own, const int32_t* pri, const uint8_t* inU, const int32_t* widx,
+                               const uint8_t* own, const int32_t* pri, const uint8_t* inU, const int32_t* nidu,
                                const int32_t* dummy_of, const int32_t* gid, const int32_t* nid,
                                const int32_t* roff, int32_t* rtgt, uint8_t* rflags, int32_t* rpri,
                                int32_t* orig_of, int cv) {
@@ -203,12 +210,10 @@ __global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int32_t*
         int32_t p = prio_of(src, n0, pri, k, cv);
         int32_t base = roff[i];
         if (src < n0) {
-            bool u = inU[src] != 0;
-            for (int32_t e = off[src]; e < off[src + 1]; ++e) {
-                int32_t t = tgt[e];
-                int32_t tp = (u && inU[t]) ? n0 + widx[t] : t;  // redirect U -> W edges to the dummy
-                rtgt[base + (e - off[src])] = nid[tp];
-            }
+            // edges from U to W go to the dummy of their target (every target of an edge from U in U is in W)
+            const int32_t* map = inU[src] ? nidu : nid;
+            const int32_t e0 = off[src], e1 = off[src + 1];
+            for (int32_t e = e0; e < e1; ++e) rtgt[base + (e - e0)] = map[tgt[e]];
             rflags[i] = (uint8_t)((own[src] ? kOwnerOdd : 0) | ((p & 1) ? kPriOdd : 0));
             orig_of[i] = src;
         } else {
@@ -478,8 +483,11 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);
     ctx->launches += 3;
     LG_TRY(exclusive_scan_i32(deg, g->off, np, nullptr, stmp2, stb2, s));
-    ++ctx->launches;
-    k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, widx, g->dummy_of,
+    int32_t* nidu;
+    LG_TRY(T.get(&nidu, n));
+    ctx->launches += 2;
+    k_nid_u<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, nid, nidu);
+    k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, nidu, g->dummy_of,
                                                   gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of, cv ? 1 : 0);
     ++ctx->launches;
     k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
