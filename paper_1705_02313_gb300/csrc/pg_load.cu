@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "pg_internal.cuh"
+#include "pg_device.cuh"
 
 namespace pg {
 namespace {
@@ -112,22 +112,6 @@ __global__ void k_trap_init(int32_t n, const int32_t* off, const int32_t* tgt, c
     }
 }
 
-// Peeling round: every vertex x that just left U decrements the count of its
-// Odd predecessors; a predecessor whose count reaches zero leaves U next.
-__global__ void k_trap_peel(int32_t nf, const int32_t* frontier, const int32_t* roff, const int32_t* radj,
-                            const uint8_t* own, uint8_t* inU, int32_t* cnt, int32_t* next, LoadScalars* sc) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = frontier[i];
-        for (int32_t r = roff[x]; r < roff[x + 1]; ++r) {
-            int32_t y = radj[r];
-            if (own[y] == 1 && atomicSub(&cnt[y], 1) == 1) {
-                inU[y] = 0;
-                next[atomicAdd(&sc->frontier, 1)] = y;
-            }
-        }
-    }
-}
-
 // W: vertices of U entered by an edge from U.
 __global__ void k_mark_w(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* inU, uint8_t* isW) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -140,6 +124,42 @@ __global__ void k_mark_w(int32_t n, const int32_t* off, const int32_t* tgt, cons
 __global__ void k_dummy_of(int32_t n, const uint8_t* isW, const int32_t* widx, int32_t* dummy_of) {
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x)
         if (isW[w]) dummy_of[widx[w]] = (int32_t)w;
+}
+
+// Peeling: every vertex x that leaves U decrements the count of its Odd
+// predecessors; a predecessor whose count reaches zero leaves U in the next
+// round. Every round runs in one cooperative launch, with a grid barrier
+// between rounds (the barrier gives up after a bounded wait and records
+// kErrBarrier). c->left[r % 3] counts round r's frontier (left[0] is the
+// initial one); round r appends the next frontier through left[(r + 1) % 3],
+// which block 0 cleared in round r - 1, and clears left[(r + 2) % 3]. The set
+// left in U does not depend on the order of the decrements.
+__global__ void __launch_bounds__(kBlock) k_trap_peel_coop(const int32_t* __restrict__ roff,
+                                                           const int32_t* __restrict__ radj,
+                                                           const uint8_t* __restrict__ own, uint8_t* inU, int32_t* cnt,
+                                                           int32_t* fa, int32_t* fb, Counters* c, int32_t max_rounds) {
+    int32_t* cur = fa;
+    int32_t* nxt = fb;
+    for (int32_t r = 0; r < max_rounds; ++r) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->left[(r + 2) % 3] = 0;
+        const int32_t nf = *(volatile int32_t*)&c->left[r % 3];
+        if (nf == 0) return;  // every block reads the same count after the barrier
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+            const int32_t x = __ldcg(cur + i);
+            for (int32_t e = roff[x]; e < roff[x + 1]; ++e) {
+                const int32_t y = radj[e];
+                if (own[y] == 1 && atomicSub(&cnt[y], 1) == 1) {
+                    inU[y] = 0;
+                    __stcg(nxt + atomicAdd(&c->left[(r + 1) % 3], 1), y);
+                }
+            }
+        }
+        if (!grid_sync(c)) return;
+        int32_t* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrJumpRounds);  // more rounds than vertices
 }
 
 // G' priority: distinct priorities (cv = 0): originals + 2k, dummy j has 2j;
@@ -341,20 +361,22 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     PG_CUDA_TRY(ctx, T.get(&fa, n));
     PG_CUDA_TRY(ctx, T.get(&fb, n));
     PG_CUDA_TRY(ctx, T.get(&inU, n));
+    Counters* pc;  // the peeling rounds' frontier counts and grid barrier
+    PG_CUDA_TRY(ctx, T.get(&pc, 1));
+    PG_CUDA_TRY(ctx, cudaMemsetAsync(pc, 0, sizeof(Counters), s));
     ++ctx->launches;
     k_trap_init<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, inU, cnt, fa, sc);
-    for (int64_t round = 0;; ++round) {
-        PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
-        PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        int32_t nf = h.frontier;
-        if (nf == 0) break;
-        if (round > n) return fail(ctx, PG_EINVAL, "pg_load_csr: trap peeling did not converge");
-        PG_CUDA_TRY(ctx, cudaMemsetAsync(&sc->frontier, 0, sizeof(int32_t), s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(&pc->left[0], &sc->frontier, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    {
+        int sms = 0, per = 0;
+        PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trap_peel_coop, kBlock, 0));
+        int blocks = std::max(1, sms * std::max(1, std::min(per, 4)));
+        int32_t max_rounds = n + 1;
+        void* args[] = {(void*)&roff, (void*)&radj, (void*)&own, (void*)&inU, (void*)&cnt,
+                        (void*)&fa,   (void*)&fb,   (void*)&pc,  (void*)&max_rounds};
         ++ctx->launches;
-        k_trap_peel<<<nblocks(nf), kBlock, 0, s>>>(nf, fa, roff, radj, own, inU, cnt, fb, sc);
-        int32_t* t = fa;
-        fa = fb;
-        fb = t;
+        PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_trap_peel_coop, blocks, kBlock, args, 0, s));
     }
     PG_CUDA_TRY(ctx, T.get(&isW, n));
     PG_CUDA_TRY(ctx, T.get(&widx, (int64_t)n + 1));
@@ -363,9 +385,12 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     k_mark_w<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, inU, isW);
     ctx->launches += 3;
     PG_CUDA_TRY(ctx, exclusive_scan_u8(isW, widx, n, stmp, stb, s));
-    int32_t k = 0;
+    int32_t k = 0, peel_err = 0;
     PG_CUDA_TRY(ctx, cudaMemcpyAsync(&k, widx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA_TRY(ctx, cudaMemcpyAsync(&peel_err, &pc->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (peel_err & kErrBarrier) return fail(ctx, PG_ECUDA, "pg_load_csr: a grid barrier of the trap peeling timed out");
+    if (peel_err) return fail(ctx, PG_EINVAL, "pg_load_csr: trap peeling did not converge");
     int64_t np = (int64_t)n + k, mp = m + k;
     if (np >= (1 << 29) - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^29 vertices after preprocessing");
     if (mp > INT32_MAX - 1) return fail(ctx, PG_EINVAL, "pg_load_csr: more than 2^31-2 edges after preprocessing");
