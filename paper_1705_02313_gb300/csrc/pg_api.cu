@@ -122,6 +122,20 @@ __device__ inline int32_t sink_id(int32_t i, const int32_t* vgame, const int32_t
     return vgame ? gsink[vgame[i]] : sink0;
 }
 
+// The initial profile of Algorithm 1 (no profile given): every Odd vertex to
+// the first edge of its list, every Even vertex and dummy to its game's sink;
+// sink slots keep their own id. In relabelled id order, coalesced.
+template <typename OffT>
+__global__ void k_default_profile(int32_t n, const OffT* __restrict__ off, const int32_t* __restrict__ tgt,
+                                  const uint8_t* __restrict__ flags, const int32_t* __restrict__ vgame,
+                                  const int32_t* __restrict__ gsink, int32_t sink0, int32_t* strat) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t f = flags[i];
+        if (f & kSinkSlot) continue;
+        strat[i] = (f & kOwnerOdd) ? tgt[off[i]] : sink_id((int32_t)i, vgame, gsink, sink0);
+    }
+}
+
 template <typename OffT>
 __global__ void k_apply_profile(int64_t n0, int32_t k, const int32_t* __restrict__ nid0,
                                 const OffT* __restrict__ off, const int32_t* __restrict__ tgt,
@@ -296,6 +310,17 @@ pg_status apply_profile(pg_game* g, const int32_t* sigma, const int32_t* tau, co
             e = cudaMemcpyAsync(b + 8 * (size_t)g->n0, dsig, (size_t)g->k, cudaMemcpyHostToDevice, s);
             dd = (const int8_t*)(b + 8 * (size_t)g->n0);
         }
+    }
+    if (!sigma && !tau && !dsig) {  // the initial profile: nothing to check, no wait
+        ctx->launches += 1;
+        if (g->off64)
+            k_default_profile<int64_t><<<grid_of(g->n), kBlock, 0, s>>>(g->n, g->off64, g->tgt, g->flags, g->vgame,
+                                                                          g->gsink, g->sink0, g->strat);
+        else
+            k_default_profile<int32_t><<<grid_of(g->n), kBlock, 0, s>>>(g->n, g->off, g->tgt, g->flags, g->vgame,
+                                                                          g->gsink, g->sink0, g->strat);
+        PG_CUDA_TRY(ctx, cudaGetLastError());
+        return PG_OK;
     }
     int32_t* err = &g->cnt->err;
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);

@@ -1510,7 +1510,8 @@ __global__ void __launch_bounds__(kBlock) k_pl_copy(int32_t np, const int32_t* _
 
 // Odd's reverse view: the in-degree of every id from Odd's edges, then each
 // edge's source (its position in Odd's view) at the next free slot of its
-// target (the order within a list is arbitrary; the lists only mark).
+// target, cur[t] starting at rv_off[t] (the order within a list is arbitrary;
+// the lists only mark).
 __global__ void __launch_bounds__(kBlock) k_rv_count(int32_t np, const int32_t* __restrict__ poff,
                                                      const int32_t* __restrict__ ptgt, int32_t* __restrict__ cnt) {
     const int32_t m = poff[np];
@@ -1519,14 +1520,11 @@ __global__ void __launch_bounds__(kBlock) k_rv_count(int32_t np, const int32_t* 
 }
 
 __global__ void __launch_bounds__(kBlock) k_rv_fill(int32_t np, const int32_t* __restrict__ poff,
-                                                    const int32_t* __restrict__ ptgt,
-                                                    const int32_t* __restrict__ rv_off, int32_t* __restrict__ cur,
+                                                    const int32_t* __restrict__ ptgt, int32_t* __restrict__ cur,
                                                     int32_t* __restrict__ rv_src) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-        for (int32_t e = poff[i]; e < poff[i + 1]; ++e) {
-            const int32_t t = ptgt[e];
-            rv_src[rv_off[t] + atomicAdd(cur + t, 1)] = i;
-        }
+        const int32_t e1 = poff[i + 1];
+        for (int32_t e = poff[i]; e < e1; ++e) rv_src[atomicAdd(cur + ptgt[e], 1)] = i;
     }
 }
 
@@ -2130,9 +2128,8 @@ pg_status build_player_split(pg_game* g) {
         PG_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s));
         k_rv_count<<<grid_for(std::max(mp_of[1], 1)), kBlock, 0, s>>>(np, g->pl_off[1], g->pl_tgt[1], cnt);
         PG_CUDA_TRY(ctx, exclusive_scan_i32(cnt, g->rv_off, n, nullptr, g->scan_tmp, g->scan_tmp_bytes, s));
-        PG_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s));
-        k_rv_fill<<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_off[1], g->pl_tgt[1], g->rv_off, cnt,
-                                                               g->rv_src);
+        PG_CUDA_TRY(ctx, cudaMemcpyAsync(cnt, g->rv_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        k_rv_fill<<<grid_for(std::max(np, 1)), kBlock, 0, s>>>(np, g->pl_off[1], g->pl_tgt[1], cnt, g->rv_src);
         PG_CUDA_TRY(ctx, cudaGetLastError());
         ctx->launches += 5;
     }

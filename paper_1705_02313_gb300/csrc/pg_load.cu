@@ -206,10 +206,22 @@ __global__ void k_assign_level(int32_t np, const uint8_t* lvl, int32_t l, int32_
     }
 }
 
-__global__ void k_relabel_degree(int32_t np, int32_t n0, const int32_t* off, const int32_t* gid, int32_t* deg) {
+// What the relabelling reads of an input vertex, packed in input order so that
+// the passes in relabelled order gather one 16-byte record per vertex: x = its
+// first edge, y = its out-degree, z = its G' priority, w = bit 0: owned by Odd,
+// bit 1: in U.
+__global__ void k_pack_vertices(int32_t n0, const int32_t* off, const uint8_t* own, const int32_t* pri,
+                                const uint8_t* inU, int32_t k, int cv, int4* rec) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e0 = off[v];
+        rec[v] = make_int4(e0, off[v + 1] - e0, prio_of(v, n0, pri, k, cv), (own[v] ? 1 : 0) | (inU[v] ? 2 : 0));
+    }
+}
+
+__global__ void k_relabel_degree(int32_t np, int32_t n0, const int4* rec, const int32_t* gid, int32_t* deg) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t src = gid[i];
-        deg[i] = src < n0 ? off[src + 1] - off[src] : 1;
+        deg[i] = src < n0 ? rec[src].y : 1;
     }
 }
 
@@ -220,21 +232,21 @@ __global__ void k_nid_u(int32_t n0, const uint8_t* isW, const int32_t* widx, con
         nidu[v] = isW[v] ? nid[n0 + widx[v]] : nid[v];
 }
 
-__global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int32_t* off, const int32_t* tgt,
-                               const uint8_t* own, const int32_t* pri, const uint8_t* inU, const int32_t* nidu,
-                               const int32_t* dummy_of, const int32_t* gid, const int32_t* nid,
+__global__ void k_relabel_rows(int32_t np, int32_t n0, int32_t k, const int4* rec, const int32_t* tgt,
+                               const int32_t* nidu, const int32_t* dummy_of, const int32_t* gid, const int32_t* nid,
                                const int32_t* roff, int32_t* rtgt, uint8_t* rflags, int32_t* rpri,
                                int32_t* orig_of, int cv) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t src = gid[i];
-        int32_t p = prio_of(src, n0, pri, k, cv);
+        int32_t p = src < n0 ? 0 : prio_of(src, n0, nullptr, k, cv);
         int32_t base = roff[i];
         if (src < n0) {
+            const int4 r = rec[src];
+            p = r.z;
             // edges from U to W go to the dummy of their target (every target of an edge from U in U is in W)
-            const int32_t* map = inU[src] ? nidu : nid;
-            const int32_t e0 = off[src], e1 = off[src + 1];
-            for (int32_t e = e0; e < e1; ++e) rtgt[base + (e - e0)] = map[tgt[e]];
-            rflags[i] = (uint8_t)((own[src] ? kOwnerOdd : 0) | ((p & 1) ? kPriOdd : 0));
+            const int32_t* map = (r.w & 2) ? nidu : nid;
+            for (int32_t j = 0; j < r.y; ++j) rtgt[base + j] = map[tgt[r.x + j]];
+            rflags[i] = (uint8_t)(((r.w & 1) ? kOwnerOdd : 0) | ((p & 1) ? kPriOdd : 0));
             orig_of[i] = src;
         } else {
             int32_t w = dummy_of[src - n0];
@@ -284,8 +296,17 @@ struct Temps {
 
 }  // namespace
 
-pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, const int32_t* tgt_in,
-                    const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out, bool with_scratch) {
+// Vertices whose priorities are checked for repeats before the load chooses its
+// mode: games with few distinct priorities repeat them within the first few
+// hundred vertices; a repeat further on is found by the ranking pass, and the
+// load then runs again in the count-vector mode.
+constexpr int32_t kDupProbe = 1 << 16;
+
+// One load; with cv_forced the count-vector mode is chosen without looking.
+// *again is set (and nothing returned) when a priority repeats beyond the probe.
+pg_status load_game_pass(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, const int32_t* tgt_in,
+                         const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out,
+                         bool with_scratch, bool cv_forced, bool* again) {
     if (!out) return fail(ctx, PG_EINVAL, "pg_load_csr: out is NULL");
     *out = nullptr;
     if (!off_in || !tgt_in || !own_in || !pri_in) return fail(ctx, PG_EINVAL, "pg_load_csr: NULL array");
@@ -323,15 +344,16 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     if (h.err & kEPri) return fail(ctx, PG_EINVAL, "pg_load_csr: negative priority");
     int32_t maxpri = h.maxpri;
 
-    // repeated priorities select the count-vector mode
-    bool cv = false;
-    {
+    // repeated priorities select the count-vector mode (probed on a prefix here)
+    bool cv = cv_forced;
+    if (!cv) {
+        const int32_t nprobe = n < kDupProbe ? n : kDupProbe;
         int64_t nwords = ((int64_t)maxpri >> 5) + 1;
         uint32_t* bits;
         PG_CUDA_TRY(ctx, T.get(&bits, nwords));
         PG_CUDA_TRY(ctx, cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)nwords, s));
         ++ctx->launches;
-        k_mark_priorities<<<nblocks(n), kBlock, 0, s>>>(n, pri, 0, n, bits, sc, 0);
+        k_mark_priorities<<<nblocks(nprobe), kBlock, 0, s>>>(nprobe, pri, 0, n, bits, sc, 0);
         PG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
         PG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         cv = (h.err & kEDup) != 0;
@@ -448,6 +470,15 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     LG_TRY(cudaMemsetAsync(&sc->err, 0, sizeof(int32_t), s));
     ++ctx->launches;
     k_mark_priorities<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, pri, cv ? 2 : 2 * k, n, bits2, sc, cv ? 1 : 0);
+    if (!cv) {  // a priority repeated beyond the probe would give two vertices one rank: load again instead
+        LG_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        LG_TRY(cudaStreamSynchronize(s));
+        if (h.err & kEDup) {
+            free_game(g);
+            *again = true;
+            return PG_OK;
+        }
+    }
     ctx->launches += 3;
     LG_TRY(exclusive_popc_scan(bits2, wprefix, nw, stmp2, stb2, s));
     if (!cv) {
@@ -505,15 +536,19 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
         }
     }
     ++ctx->launches;
-    k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, off, gid, deg);
+    int4* rec;
+    LG_TRY(T.get(&rec, n));
+    ++ctx->launches;
+    k_pack_vertices<<<nblocks(n), kBlock, 0, s>>>(n, off, own, pri, inU, k, cv ? 1 : 0, rec);
+    k_relabel_degree<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, rec, gid, deg);
     ctx->launches += 3;
     LG_TRY(exclusive_scan_i32(deg, g->off, np, nullptr, stmp2, stb2, s));
     int32_t* nidu;
     LG_TRY(T.get(&nidu, n));
     ctx->launches += 2;
     k_nid_u<<<nblocks(n), kBlock, 0, s>>>(n, isW, widx, nid, nidu);
-    k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, off, tgt, own, pri, inU, nidu, g->dummy_of,
-                                                  gid, nid, g->off, g->tgt, g->flags, g->pri, g->orig_of, cv ? 1 : 0);
+    k_relabel_rows<<<nblocks(np), kBlock, 0, s>>>((int32_t)np, n, k, rec, tgt, nidu, g->dummy_of, gid, nid, g->off,
+                                                  g->tgt, g->flags, g->pri, g->orig_of, cv ? 1 : 0);
     ++ctx->launches;
     k_maps<<<nblocks(np), kBlock, 0, s>>>(n, k, nid, g->nid0, g->dnid);
     // the sink slot: no edges, a flag, no priority or original vertex
@@ -549,6 +584,14 @@ pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, co
     }
     *out = g;
     return PG_OK;
+}
+
+pg_status load_game(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_in, const int32_t* tgt_in,
+                    const uint8_t* own_in, const int32_t* pri_in, int32_t mem_kind, pg_game** out, bool with_scratch) {
+    bool again = false;
+    pg_status st = load_game_pass(ctx, n, m, off_in, tgt_in, own_in, pri_in, mem_kind, out, with_scratch, false, &again);
+    if (st != PG_OK || !again) return st;
+    return load_game_pass(ctx, n, m, off_in, tgt_in, own_in, pri_in, mem_kind, out, with_scratch, true, &again);
 }
 
 }  // namespace pg

@@ -204,6 +204,16 @@ def test_cv_limits(pg, ctx):
         assert pg.pg_game_levels(game).size == 5 and pg.pg_game_info(game)[2] == 0
     finally:
         pg.pg_game_free(game)
+    # the load probes the first 2^16 priorities for repeats; a repeat further on is found when the priorities
+    # are ranked, and the load runs again in the count-vector mode (refused here: 70,000 distinct values)
+    g = gen.random_game(70_000, 1, 3, seed=4)
+    pri = g.pri.copy()
+    pri[-1] = pri[-2]
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_load_csr(ctx, g.n, g.m, g.offsets, g.targets, g.owner, pri)
+    assert e.value.code == pg.PG_EUNSUPPORTED
+    game = pg.pg_load_csr(ctx, g.n, g.m, *g.arrays())  # the distinct game itself still loads
+    pg.pg_game_free(game)
     # each level's digit is one bit wider than the bit length of the level's size: 5 levels of 2^24 / 5 ids
     # take 5 x 23 bits, within the key's 126
     n = (1 << 24)
