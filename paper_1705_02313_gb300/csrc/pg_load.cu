@@ -126,7 +126,47 @@ __global__ void k_dummy_of(int32_t n, const uint8_t* isW, const int32_t* widx, i
         if (isW[w]) dummy_of[widx[w]] = (int32_t)w;
 }
 
-// Peeling: every vertex x that leaves U decrements the count of its Odd
+// Peeling without rounds: every vertex x that leaves U decrements the count of
+// its Odd predecessors, and a predecessor whose count reaches zero leaves U
+// too. Each thread takes vertices of the initial frontier and peels what they
+// free depth first, keeping up to kPeelStack vertices of its own and peeling at
+// most kPeelBudget per frontier vertex; a vertex freed beyond either goes to the
+// overflow list (counted in c->left[0]), which k_trap_peel_coop then peels in
+// rounds across the grid (a large cascade must not run in one thread). The set
+// left in U does not depend on the order of the decrements.
+constexpr int kPeelStack = 16;
+constexpr int kPeelBudget = 64;
+
+__global__ void __launch_bounds__(kBlock) k_trap_peel_dfs(const int32_t* __restrict__ frontier, const LoadScalars* sc,
+                                                          const int32_t* __restrict__ roff,
+                                                          const int32_t* __restrict__ radj,
+                                                          const uint8_t* __restrict__ own, uint8_t* inU, int32_t* cnt,
+                                                          int32_t* overflow, Counters* c) {
+    const int32_t nf = sc->frontier;
+    int32_t stack[kPeelStack];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        int32_t top = 0, budget = kPeelBudget;
+        stack[top++] = frontier[i];
+        while (top > 0) {
+            const int32_t x = stack[--top];
+            if (--budget < 0) {  // the rest of this cascade is peeled in rounds
+                overflow[atomicAdd(&c->left[0], 1)] = x;
+                continue;
+            }
+            const int32_t e1 = roff[x + 1];
+            for (int32_t e = roff[x]; e < e1; ++e) {
+                const int32_t y = radj[e];
+                if (own[y] == 1 && atomicSub(&cnt[y], 1) == 1) {
+                    inU[y] = 0;
+                    if (top < kPeelStack) stack[top++] = y;
+                    else overflow[atomicAdd(&c->left[0], 1)] = y;
+                }
+            }
+        }
+    }
+}
+
+// Peeling in rounds: every vertex x that leaves U decrements the count of its Odd
 // predecessors; a predecessor whose count reaches zero leaves U in the next
 // round. Every round runs in one cooperative launch, with a grid barrier
 // between rounds (the barrier gives up after a bounded wait and records
@@ -388,15 +428,16 @@ pg_status load_game_pass(pg_ctx* ctx, int32_t n, int64_t m, const int32_t* off_i
     PG_CUDA_TRY(ctx, cudaMemsetAsync(pc, 0, sizeof(Counters), s));
     ++ctx->launches;
     k_trap_init<<<nblocks(n), kBlock, 0, s>>>(n, off, tgt, own, inU, cnt, fa, sc);
-    PG_CUDA_TRY(ctx, cudaMemcpyAsync(&pc->left[0], &sc->frontier, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    {
+    ++ctx->launches;
+    k_trap_peel_dfs<<<nblocks(n), kBlock, 0, s>>>(fa, sc, roff, radj, own, inU, cnt, fb, pc);
+    {  // the overflow list (in fb), if any, in rounds
         int sms = 0, per = 0;
         PG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
         PG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trap_peel_coop, kBlock, 0));
         int blocks = std::max(1, sms * std::max(1, std::min(per, 4)));
         int32_t max_rounds = n + 1;
         void* args[] = {(void*)&roff, (void*)&radj, (void*)&own, (void*)&inU, (void*)&cnt,
-                        (void*)&fa,   (void*)&fb,   (void*)&pc,  (void*)&max_rounds};
+                        (void*)&fb,   (void*)&fa,   (void*)&pc,  (void*)&max_rounds};
         ++ctx->launches;
         PG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void*)k_trap_peel_coop, blocks, kBlock, args, 0, s));
     }
