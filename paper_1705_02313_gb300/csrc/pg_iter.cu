@@ -227,42 +227,37 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, c
          tile += nwarps) {
         if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP];
-        uint32_t d[ILP];  // steps; bit 16: v's priority is odd
-        bool act[ILP], slotid[ILP];
+        uint32_t slots = 0, odd = 0, act = 0;  // bit j: slot j's id is a sink slot / has an odd priority / walks
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
             const uint8_t fv = v[j] < n ? flags[v[j]] : 0;
-            slotid[j] = (fv & kSinkSlot) != 0;
-            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
-            d[j] = 1u | ((fv & kPriOdd) ? 0x10000u : 0u);
+            if (fv & kSinkSlot) slots |= 1u << j;
+            if (fv & kPriOdd) odd |= 1u << j;
+            x[j] = (v[j] < n && !(fv & kSinkSlot)) ? __ldg(strat + v[j]) : INT32_MAX;
+            if (v[j] < n && !(fv & kSinkSlot) && x[j] < v[j]) act |= 1u << j;
         }
-#pragma unroll
-        for (int j = 0; j < ILP; ++j) act[j] = v[j] < n && !slotid[j] && x[j] < v[j] && (d[j] & 0xffffu) < cap;
-        for (;;) {
-            bool any = false;
+        // the walks start together, so a walk still going has read `steps` successors
+        for (uint32_t steps = 1; act && steps < cap; ++steps) {
             int32_t nx[ILP];
 #pragma unroll
-            for (int j = 0; j < ILP; ++j) nx[j] = act[j] ? __ldg(strat + x[j]) : x[j];
+            for (int j = 0; j < ILP; ++j) nx[j] = ((act >> j) & 1u) ? __ldg(strat + x[j]) : x[j];
 #pragma unroll
             for (int j = 0; j < ILP; ++j) {
-                if (act[j]) {
+                if ((act >> j) & 1u) {
                     x[j] = nx[j];
-                    ++d[j];
-                    act[j] = x[j] < v[j] && (d[j] & 0xffffu) < cap;
+                    if (x[j] >= v[j]) act &= ~(1u << j);
                 }
-                any |= act[j];
             }
-            if (!any) break;
         }
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             bool pend = false;
             if (v[j] < n) {
                 uint32_t w;
-                if (slotid[j]) w = kG32Sink;  // a sink slot: inert (its own top, even)
+                if ((slots >> j) & 1u) w = kG32Sink;  // a sink slot: inert (its own top, even)
                 else if (x[j] > v[j])
-                    w = x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink | (d[j] >> 16) : (uint32_t)x[j];
+                    w = x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink | ((odd >> j) & 1u) : (uint32_t)x[j];
                 else if (x[j] == v[j]) w = kG32None | (uint32_t)v[j];  // v is its cycle's maximum
                 else {
                     w = kG32Pend | (uint32_t)x[j];
@@ -1266,57 +1261,54 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
         if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
-        int32_t v[ILP], x[ILP], len[ILP];
+        int32_t v[ILP], x[ILP];
         uint32_t w0[ILP], ot[ILP];
-        bool act[ILP], top[ILP];
+        uint32_t act = 0, top = 0, podd = 0;  // bit j: slot j walks / is TOP / its top's priority is odd
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
-            len[j] = 0;
             const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
             w0[j] = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
-            top[j] = g32_none(w0[j]);
+            if (g32_none(w0[j])) top |= 1u << j;
             x[j] = g32_sink(w0[j]) ? v[j] : g32_ptr(w0[j]);  // a child of the sink is its own top
-            act[j] = !(w0[j] & (kG32None | kG32Sink));
-            if (g32_sink(w0[j])) len[j] = (int32_t)((w0[j] & 1u) << 30);  // once a chain ends: its top's parity
+            if (!(w0[j] & (kG32None | kG32Sink))) act |= 1u << j;
+            if (g32_sink(w0[j])) podd |= (w0[j] & 1u) << j;
             if (v[j] < n && g32_none(w0[j]) && x[j] == v[j] && (flags[v[j]] & kPriOdd))
                 atomicAdd(&gst[vgame ? vgame[v[j]] : 0].nodd, 1);
         }
-        for (;;) {
-            bool any = false;
+        // the chains start together, so a chain still going has taken `len` steps
+        for (int32_t len = 1; act; ++len) {
+            if (len > deep_cut) {  // a deep forest: the iteration is abandoned (loop stops)
+                cnt->deep = 1;
+                break;
+            }
             uint32_t wx[ILP];
 #pragma unroll
-            for (int j = 0; j < ILP; ++j) wx[j] = act[j] ? gd32[x[j]] : 0u;
+            for (int j = 0; j < ILP; ++j) wx[j] = ((act >> j) & 1u) ? gd32[x[j]] : 0u;
 #pragma unroll
             for (int j = 0; j < ILP; ++j) {
-                if (act[j] && ++len[j] > deep_cut) {  // a deep forest: the iteration is abandoned (loop stops)
-                    act[j] = false;
-                    cnt->deep = 1;
+                if (!((act >> j) & 1u)) continue;
+                if (wx[j] & kG32Top) {  // a none vertex, or one already marked TOP
+                    top |= 1u << j;
+                    act &= ~(1u << j);
+                } else if (g32_sink(wx[j])) {  // x is the top
+                    podd |= (wx[j] & 1u) << j;
+                    act &= ~(1u << j);
+                } else {
+                    const int32_t nx = g32_ptr(wx[j]);
+                    if (nx <= x[j]) act &= ~(1u << j);  // g-chains rise (a guard, never taken here)
+                    x[j] = nx;
                 }
-                if (act[j]) {
-                    if (wx[j] & kG32Top) {  // a none vertex, or one already marked TOP
-                        top[j] = true;
-                        act[j] = false;
-                    } else if (g32_sink(wx[j])) {  // x is the top
-                        len[j] = (int32_t)((wx[j] & 1u) << 30);
-                        act[j] = false;
-                    } else {
-                        const int32_t nx = g32_ptr(wx[j]);
-                        act[j] = nx > x[j];  // g-chains rise (a guard, never false here)
-                        x[j] = nx;
-                    }
-                }
-                any |= act[j];
             }
-            if (!any) break;
         }
 #pragma unroll
         for (int j = 0; j < ILP; ++j) ot[j] = (omark && v[j] < n) ? topw[v[j]] : 0u;
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
-            if (top[j] && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
-            const uint32_t tw = top[j] ? kG32Top : ((len[j] >> 30) & 1 ? kTopOdd : 0u) | (uint32_t)x[j];
+            const bool tp = (top >> j) & 1u;
+            if (tp && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
+            const uint32_t tw = tp ? kG32Top : (((podd >> j) & 1u) ? kTopOdd : 0u) | (uint32_t)x[j];
             if (!omark) {
                 topw[v[j]] = tw;
             } else if (tw != ot[j]) {
