@@ -1262,18 +1262,19 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
          tile += nwarps) {
         if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP];
-        uint32_t w0[ILP], ot[ILP];
-        uint32_t act = 0, top = 0, podd = 0;  // bit j: slot j walks / is TOP / its top's priority is odd
+        uint32_t ot[ILP];
+        // bit j: slot j walks / is TOP / its top's priority is odd / its own word is "none" (not to be marked)
+        uint32_t act = 0, top = 0, podd = 0, wnone = 0;
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
             const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
-            w0[j] = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
-            if (g32_none(w0[j])) top |= 1u << j;
-            x[j] = g32_sink(w0[j]) ? v[j] : g32_ptr(w0[j]);  // a child of the sink is its own top
-            if (!(w0[j] & (kG32None | kG32Sink))) act |= 1u << j;
-            if (g32_sink(w0[j])) podd |= (w0[j] & 1u) << j;
-            if (v[j] < n && g32_none(w0[j]) && x[j] == v[j] && (flags[v[j]] & kPriOdd))
+            const uint32_t w0 = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
+            if (g32_none(w0)) top |= 1u << j, wnone |= 1u << j;
+            x[j] = g32_sink(w0) ? v[j] : g32_ptr(w0);  // a child of the sink is its own top
+            if (!(w0 & (kG32None | kG32Sink))) act |= 1u << j;
+            if (g32_sink(w0)) podd |= (w0 & 1u) << j;
+            if (v[j] < n && g32_none(w0) && x[j] == v[j] && (flags[v[j]] & kPriOdd))
                 atomicAdd(&gst[vgame ? vgame[v[j]] : 0].nodd, 1);
         }
         // the chains start together, so a chain still going has taken `len` steps
@@ -1307,7 +1308,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
         for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
             const bool tp = (top >> j) & 1u;
-            if (tp && !g32_none(w0[j])) gd32[v[j]] = w0[j] | kG32Top;
+            if (tp && !((wnone >> j) & 1u)) gd32[v[j]] |= kG32Top;  // only this thread writes v's word
             const uint32_t tw = tp ? kG32Top : (((podd >> j) & 1u) ? kTopOdd : 0u) | (uint32_t)x[j];
             if (!omark) {
                 topw[v[j]] = tw;
