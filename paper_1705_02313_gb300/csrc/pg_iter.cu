@@ -1526,23 +1526,24 @@ __global__ void __launch_bounds__(kBlock) k_rv_fill(int32_t np, const int32_t* _
 // decision took a chain comparison (two finite successors with the best top
 // so far), *gi is its game. Vertices of games that do not switch this player
 // now are left alone (tie set, no switch).
-__device__ inline bool switch_at(int32_t i, int player, const int32_t* __restrict__ vid,
+template <int PLAYER, bool BATCH>
+__device__ inline bool switch_at(int32_t i, const int32_t* __restrict__ vid,
                                  const int32_t* __restrict__ poff, const int32_t* __restrict__ ptgt,
                                  const uint8_t* __restrict__ flags, const uint32_t* __restrict__ gd32,
                                  const uint32_t* __restrict__ topw, const int32_t* __restrict__ vgame,
                                  const int32_t* __restrict__ gsink, int32_t sink0, const GameState* gst,
                                  int32_t* strat, bool* tie_out, int32_t* gi_out) {
     const int32_t v = vid[i];
-    const int32_t gi = vgame ? vgame[v] : 0;
+    const int32_t gi = BATCH ? vgame[v] : 0;
     *gi_out = gi;
     *tie_out = true;
-    if (vgame) {
+    if (BATCH) {
         const GameState st = gst[gi];
-        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return false;
+        if (st.phase != kPhaseActive || (PLAYER == 0 && st.sw_odd != 0)) return false;
     }
     const int32_t e0 = poff[i], e1 = poff[i + 1];
     const int32_t cur = strat[v];
-    const int32_t sk = player == 0 ? (vgame ? gsink[gi] : sink0) : -1;
+    const int32_t sk = PLAYER == 0 ? (BATCH ? gsink[gi] : sink0) : -1;
     int32_t best = sk;  // Even: the sink first; Odd: none yet
     uint32_t tbest = 0;
     bool cur_top = false, tie = false;
@@ -1556,9 +1557,9 @@ __device__ inline bool switch_at(int32_t i, int player, const int32_t* __restric
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (t[j] < 0) continue;
-            if (t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
+            if (PLAYER == 0 && t[j] == cur) cur_top = (tt[j] & kG32Top) != 0;
             bool take;
-            if (player == 1) {
+            if (PLAYER == 1) {
                 tie |= best >= 0 && !((tt[j] | tbest) & kG32Top) && top_id(tt[j]) == top_id(tbest);
                 take = best < 0 || cmp_val(t[j], tt[j], best, tbest, gd32, flags) < 0;
             } else take = (best == sk ? cmp_sink(tt[j]) : cmp_val(t[j], tt[j], best, tbest, gd32, flags)) > 0;
@@ -1569,21 +1570,21 @@ __device__ inline bool switch_at(int32_t i, int player, const int32_t* __restric
         }
     }
     *tie_out = tie;
-    const bool sw = best != cur && (player == 0 ? !cur_top : !(tbest & kG32Top));
+    const bool sw = best != cur && (PLAYER == 0 ? !cur_top : !(tbest & kG32Top));
     if (sw) strat[v] = best;
     return sw;
 }
 
 // A switch counted into its game (packed games: one atomic per group of
 // lanes of the same game; one game: the block total at the end).
-__device__ inline void count_switch(bool sw, int32_t gi, int player, const int32_t* vgame, GameState* gst,
-                                    int32_t* nsw) {
+template <int PLAYER, bool BATCH>
+__device__ inline void count_switch(bool sw, int32_t gi, GameState* gst, int32_t* nsw) {
     if (!sw) return;
     ++*nsw;
-    if (vgame) {
+    if (BATCH) {
         cg::coalesced_group swg = cg::coalesced_threads();
         cg::coalesced_group same = cg::labeled_partition(swg, gi);
-        if (same.thread_rank() == 0) atomicAdd(player ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
+        if (same.thread_rank() == 0) atomicAdd(PLAYER ? &gst[gi].sw_odd : &gst[gi].sw_even, (int32_t)same.size());
     }
 }
 
@@ -1594,8 +1595,8 @@ __device__ inline void count_switch(bool sw, int32_t gi, int player, const int32
 // comparison; a full pass (the first of a call, or after an SI-Reset:
 // *full_flag != 0) evaluates every vertex and sets each mark to that flag.
 // Full occupancy (32 registers): the evaluations wait on their gathers.
-template <int BS, bool MARKS>
-__global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int player, const int32_t* __restrict__ vid,
+template <int BS, int PLAYER, bool MARKS, bool BATCH>
+__global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, const int32_t* __restrict__ vid,
                                                       const int32_t* __restrict__ poff,
                                                       const int32_t* __restrict__ ptgt,
                                                       const uint8_t* __restrict__ flags,
@@ -1606,9 +1607,9 @@ __global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int
                                                       GameState* gst, int32_t* strat, Counters* cnt,
                                                       uint8_t* omark, const int32_t* __restrict__ full_flag) {
     if (cnt->err || cnt->deep) return;  // unfinished jumping, or a deep forest (the loop stops)
-    if (!vgame) {  // one game: the whole pass is skipped when the game does not switch this player now
+    if (!BATCH) {  // one game: the whole pass is skipped when the game does not switch this player now
         const GameState st = gst[0];
-        if (st.phase != kPhaseActive || (player == 0 && st.sw_odd != 0)) return;
+        if (st.phase != kPhaseActive || (PLAYER == 0 && st.sw_odd != 0)) return;
     }
     const bool full = !MARKS || *full_flag;
     int32_t nsw = 0;
@@ -1616,10 +1617,10 @@ __global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int
         for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
             bool tie;
             int32_t gi;
-            const bool sw = switch_at(i, player, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0, gst, strat,
-                                      &tie, &gi);
+            const bool sw = switch_at<PLAYER, BATCH>(i, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0, gst,
+                                                     strat, &tie, &gi);
             if (MARKS) omark[i] = tie;
-            count_switch(sw, gi, player, vgame, gst, &nsw);
+            count_switch<PLAYER, BATCH>(sw, gi, gst, &nsw);
         }
     } else if (MARKS) {
         // warps take 512 positions at a time: each lane loads 16 marks, the marked positions are listed in
@@ -1653,16 +1654,16 @@ __global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int
                 const int32_t i = mine[j];  // < np: the padding is never marked
                 bool tie;
                 int32_t gi;
-                const bool sw = switch_at(i, player, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0, gst,
-                                          strat, &tie, &gi);
+                const bool sw = switch_at<PLAYER, BATCH>(i, vid, poff, ptgt, flags, gd32, topw, vgame, gsink, sink0,
+                                                         gst, strat, &tie, &gi);
                 if (!tie) omark[i] = 0;
-                count_switch(sw, gi, player, vgame, gst, &nsw);
+                count_switch<PLAYER, BATCH>(sw, gi, gst, &nsw);
             }
             __syncwarp();
         }
     }
     block_add(nsw, &cnt->n_switch);
-    if (!vgame) {  // one game: the block totals are the game's
+    if (!BATCH) {  // one game: the block totals are the game's
         __shared__ int32_t tot;
         if (threadIdx.x == 0) tot = 0;
         __syncthreads();
@@ -1671,7 +1672,7 @@ __global__ void __launch_bounds__(BS, 2048 / BS) k_switch_cmp_pl(int32_t np, int
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
         if ((threadIdx.x & 31) == 0 && x) atomicAdd(&tot, x);
         __syncthreads();
-        if (threadIdx.x == 0 && tot) atomicAdd(player ? &gst[0].sw_odd : &gst[0].sw_even, tot);
+        if (threadIdx.x == 0 && tot) atomicAdd(PLAYER ? &gst[0].sw_odd : &gst[0].sw_even, tot);
     }
 }
 
@@ -1997,8 +1998,11 @@ void launch_switch_cmp_bs(pg_game* g, int player) {
         const int64_t wave = (int64_t)std::max(sms, 1) * (2048 / BS);
         const int64_t b = std::max<int64_t>(1, std::min<int64_t>((np + BS - 1) / BS, wave));
         uint8_t* om = player == 1 ? omark_of(g) : nullptr;
-        auto kern = om ? k_switch_cmp_pl<BS, true> : k_switch_cmp_pl<BS, false>;
-        kern<<<(unsigned)b, BS, 0, s>>>((int32_t)np, player, g->pl_vid[player], g->pl_off[player], g->pl_tgt[player],
+        const bool batch = g->vgame != nullptr;
+        auto kern = player == 0 ? (batch ? k_switch_cmp_pl<BS, 0, false, true> : k_switch_cmp_pl<BS, 0, false, false>)
+                    : om        ? (batch ? k_switch_cmp_pl<BS, 1, true, true> : k_switch_cmp_pl<BS, 1, true, false>)
+                                : (batch ? k_switch_cmp_pl<BS, 1, false, true> : k_switch_cmp_pl<BS, 1, false, false>);
+        kern<<<(unsigned)b, BS, 0, s>>>((int32_t)np, g->pl_vid[player], g->pl_off[player], g->pl_tgt[player],
                                         g->flags, g->gd32, topw, g->vgame, g->gsink, g->sink0, g->gst, g->strat,
                                         g->cnt, om, g->gactive + 1);
         return;
