@@ -214,7 +214,7 @@ __device__ inline bool tile_idle(int64_t t0, int64_t t1, int32_t n, const int32_
     return a == b && gst[a].phase != kPhaseActive;
 }
 
-template <uint32_t cap, int ILP = kIlp>
+template <uint32_t cap, int ILP = kIlp, bool BATCH = false>
 __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, const int32_t* __restrict__ strat,
                                                      const uint8_t* __restrict__ flags,
                                                      const int32_t* __restrict__ vgame,
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, c
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; (tile * 32 * ILP) < n;
          tile += nwarps) {
-        if (tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
+        if (BATCH && tile_idle(tile * 32 * ILP, (tile + 1) * 32 * ILP, n, vgame, gst)) continue;
         int32_t v[ILP], x[ILP];
         uint32_t slots = 0, odd = 0, act = 0;  // bit j: slot j's id is a sink slot / has an odd priority / walks
 #pragma unroll
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, c
                 uint32_t w;
                 if ((slots >> j) & 1u) w = kG32Sink;  // a sink slot: inert (its own top, even)
                 else if (x[j] > v[j])
-                    w = x[j] == sink_of(v[j], vgame, gsink, sink0) ? kG32Sink | ((odd >> j) & 1u) : (uint32_t)x[j];
+                    w = x[j] == (BATCH ? gsink[vgame[v[j]]] : sink0) ? kG32Sink | ((odd >> j) & 1u) : (uint32_t)x[j];
                 else if (x[j] == v[j]) w = kG32None | (uint32_t)v[j];  // v is its cycle's maximum
                 else {
                     w = kG32Pend | (uint32_t)x[j];
@@ -1953,11 +1953,12 @@ pg_status enqueue_valuation_cmp(pg_game* g) {
     PG_CUDA_TRY(ctx, cudaMemsetAsync(c, 0, sizeof(Counters), s));
     prof_begin(g, KID_WALK);
     {
-        auto walk = k_walk_cmp<kWalkCap, PG_CHAIN_ILP>;
+        const bool batch = g->vgame != nullptr;
+        auto walk = batch ? k_walk_cmp<kWalkCap, PG_CHAIN_ILP, true> : k_walk_cmp<kWalkCap, PG_CHAIN_ILP, false>;
         switch (g->tune.walk_cap) {
-            case 16: walk = k_walk_cmp<16, PG_CHAIN_ILP>; break;
-            case 32: walk = k_walk_cmp<32, PG_CHAIN_ILP>; break;
-            case 128: walk = k_walk_cmp<128, PG_CHAIN_ILP>; break;
+            case 16: walk = batch ? k_walk_cmp<16, PG_CHAIN_ILP, true> : k_walk_cmp<16, PG_CHAIN_ILP, false>; break;
+            case 32: walk = batch ? k_walk_cmp<32, PG_CHAIN_ILP, true> : k_walk_cmp<32, PG_CHAIN_ILP, false>; break;
+            case 128: walk = batch ? k_walk_cmp<128, PG_CHAIN_ILP, true> : k_walk_cmp<128, PG_CHAIN_ILP, false>; break;
             default: break;
         }
         walk<<<ilp_grid(n), kBlock, 0, s>>>(n, g->strat, g->flags, g->vgame, g->gsink, g->sink0, g->gd32, g->plist,
