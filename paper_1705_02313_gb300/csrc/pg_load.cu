@@ -30,7 +30,8 @@ inline unsigned nblocks(int64_t n, int per = kBlock) {
 __global__ void k_validate(int32_t n, int64_t m, const int32_t* off, const int32_t* tgt, const uint8_t* own,
                            const int32_t* pri, LoadScalars* sc) {
     int32_t err = 0, mx = -1;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = tid; v < n; v += nthr) {
         int32_t a = off[v], b = off[v + 1];
         if (b <= a || a < 0 || (int64_t)b > m) err |= kEOff;
         if (v == 0 && a != 0) err |= kEOff;
@@ -38,12 +39,19 @@ __global__ void k_validate(int32_t n, int64_t m, const int32_t* off, const int32
         if (own[v] > 1) err |= kEOwn;
         if (pri[v] < 0) err |= kEPri;
         if (pri[v] > mx) mx = pri[v];
-        if (!(err & kEOff))
-            for (int32_t e = a; e < b; ++e)
-                if (tgt[e] < 0 || tgt[e] >= n) err |= kETgt;
     }
-    if (err) atomicOr(&sc->err, err);
-    atomicMax(&sc->maxpri, mx);
+    for (int64_t e = tid; e < m; e += nthr)  // every target, in order (the array holds m whatever the offsets)
+        if (tgt[e] < 0 || tgt[e] >= n) err |= kETgt;
+    // one atomic of each kind per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        err |= __shfl_xor_sync(0xffffffffu, err, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (err) atomicOr(&sc->err, err);
+        atomicMax(&sc->maxpri, mx);
+    }
 }
 
 // Marks every priority in a bitmap; a bit already set means a repeated priority.
@@ -99,16 +107,25 @@ __global__ void k_reverse_scatter(int32_t n, const int32_t* off, const int32_t* 
 // vertices without such an edge leave U first.
 __global__ void k_trap_init(int32_t n, const int32_t* off, const int32_t* tgt, const uint8_t* own, uint8_t* inU,
                             int32_t* cnt, int32_t* frontier, LoadScalars* sc) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        if (own[v] != 1) {
-            inU[v] = 0;
-            continue;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform rounds (the frontier is appended one atomic per warp)
+    for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; b < n; b += stride) {
+        const int64_t v = b + lane;
+        bool push = false;
+        if (v < n) {
+            if (own[v] != 1) {
+                inU[v] = 0;
+            } else {
+                int32_t c = 0;
+                for (int32_t e = off[v]; e < off[v + 1]; ++e) c += own[tgt[e]] == 1;
+                cnt[v] = c;
+                inU[v] = c > 0;
+                push = c == 0;
+            }
         }
-        int32_t c = 0;
-        for (int32_t e = off[v]; e < off[v + 1]; ++e) c += own[tgt[e]] == 1;
-        cnt[v] = c;
-        inU[v] = c > 0;
-        if (c == 0) frontier[atomicAdd(&sc->frontier, 1)] = (int32_t)v;
+        const int32_t slot = warp_append(push, &sc->frontier);
+        if (push) frontier[slot] = (int32_t)v;
     }
 }
 
