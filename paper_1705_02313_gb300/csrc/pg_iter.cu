@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_cmp(int32_t n, c
             const uint8_t fv = v[j] < n ? flags[v[j]] : 0;
             if (fv & kSinkSlot) slots |= 1u << j;
             if (fv & kPriOdd) odd |= 1u << j;
-            x[j] = (v[j] < n && !(fv & kSinkSlot)) ? __ldg(strat + v[j]) : INT32_MAX;
+            // read together with the flags (a sink slot's successor is itself, so its walk ends at once)
+            x[j] = v[j] < n ? __ldg(strat + v[j]) : INT32_MAX;
             if (v[j] < n && !(fv & kSinkSlot) && x[j] < v[j]) act |= 1u << j;
         }
         // the walks start together, so a walk still going has read `steps` successors
@@ -1268,8 +1269,8 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             v[j] = (int32_t)((tile * 32 * ILP) + lane + 32 * j);
-            const bool slotid = v[j] < n && (flags[v[j]] & kSinkSlot);
-            const uint32_t w0 = (v[j] < n && !slotid) ? gd32[v[j]] : kG32Sink;
+            // (a sink slot's word is the sink bit alone: its own top, even)
+            const uint32_t w0 = v[j] < n ? gd32[v[j]] : kG32Sink;
             if (g32_none(w0)) top |= 1u << j, wnone |= 1u << j;
             x[j] = g32_sink(w0) ? v[j] : g32_ptr(w0);  // a child of the sink is its own top
             if (!(w0 & (kG32None | kG32Sink))) act |= 1u << j;
