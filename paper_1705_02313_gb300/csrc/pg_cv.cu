@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(kBlock) k_walk_cv(int32_t n, Levels L, const i
 #pragma unroll
         for (int j = 0; j < kIlpCv; ++j) {
             v[j] = (int32_t)(tile * 32 * kIlpCv + lane + 32 * j);
+            const int32_t xr = v[j] < n ? __ldg(strat + v[j]) : INT32_MAX;  // loaded with the flags, not after
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
-            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
+            x[j] = slotid[j] ? INT32_MAX : xr;
             d[j] = 1;
             acc[j] = (v[j] < n && !slotid[j]) ? count_one(L, v[j]) : 0;
             act[j] = v[j] < n && !slotid[j] && x[j] < v[j];
@@ -370,8 +371,9 @@ __global__ void __launch_bounds__(kBlock) k_chain_cv(int32_t n, const uint32_t* 
 #pragma unroll
         for (int j = 0; j < kIlpCv; ++j) {
             v[j] = (int32_t)(tile * 32 * kIlpCv + lane + 32 * j);
+            const uint32_t wr = v[j] < n ? gd32[v[j]] : 0x40000000u;  // loaded with the flags, not after them
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
-            const uint32_t w = (v[j] < n && !slotid[j]) ? gd32[v[j]] : 0x40000000u;
+            const uint32_t w = slotid[j] ? 0x40000000u : wr;
             cyc[j] = w32_none(w) ? w32_ptr(w) : -1;
             acc[j] = (v[j] < n && !slotid[j] && cyc[j] < 0) ? ws[v[j]] : 0;
             x[j] = w32_ptr(w);

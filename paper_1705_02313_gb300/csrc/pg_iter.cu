@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(kBlock) k_walk(int32_t n, const int32_t* __res
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             v[j] = (int32_t)(warp_tile_base(tile) + lane + 32 * j);
+            const int32_t xr = v[j] < n ? __ldg(strat + v[j]) : INT32_MAX;  // loaded with the flags, not after
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
-            x[j] = (v[j] < n && !slotid[j]) ? __ldg(strat + v[j]) : INT32_MAX;
+            x[j] = slotid[j] ? INT32_MAX : xr;
             d[j] = 1;
         }
 #pragma unroll
@@ -394,8 +395,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_chain1(int32_t n, const uint32_t*
 #pragma unroll
         for (int j = 0; j < kIlpChain1; ++j) {
             v[j] = (int32_t)((tile * 32 * kIlpChain1) + lane + 32 * j);
+            const uint32_t wr = v[j] < n ? gd32[v[j]] : kG32Sink;  // loaded with the flags, not after them
             slotid[j] = v[j] < n && (flags[v[j]] & kSinkSlot);
-            const uint32_t w = (v[j] < n && !slotid[j]) ? gd32[v[j]] : kG32Sink;
+            const uint32_t w = slotid[j] ? kG32Sink : wr;
             g[j] = g32_ptr(w);
             sinkchild[j] = g32_sink(w);
             cyc[j] = g32_none(w) ? g[j] : -1;
