@@ -1306,7 +1306,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock)
             }
         }
 #pragma unroll
-        for (int j = 0; j < ILP; ++j) ot[j] = (omark && v[j] < n) ? topw[v[j]] : 0u;
+        for (int j = 0; j < ILP; ++j) ot[j] = (omark && v[j] < n) ? __ldcs(topw + v[j]) : 0u;  // read once: evict first
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
             if (v[j] >= n) continue;
