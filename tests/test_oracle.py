@@ -277,6 +277,92 @@ def test_literal_compare_walk_matches_ranks():
             assert o2.compare(gp, strat, r["depth"], u, w) == np.sign(key[u] - key[w])
 
 
+def play_tops(gp, strat, cls):
+    """Top of every finite vertex by its plain definition: the vertex with the
+    largest priority on its play before the sink (-1 for the others)."""
+    n, pri = gp["n"], gp["pri"]
+    top = np.full(n, -1, np.int64)
+    for v in range(n):
+        if cls[v] != o2.FIN:
+            continue
+        x, best = v, v
+        while x != n:
+            if pri[x] > pri[best]:
+                best = x
+            x = strat[x]
+        top[v] = best
+    return top
+
+
+def test_different_tops_decide_by_the_larger_tops_parity():
+    # Section 3's order (Maxdiff): when two finite plays have different tops, the larger one is on one play only
+    # and above everything on the other, so it decides by its parity; against the sink's empty valuation a finite
+    # play is better for Even exactly when its top is even. The loop's comparisons use this on top words.
+    rng = np.random.default_rng(21)
+    checked = 0
+    for s, g in small_games(12, 30, 400, 1, 4, base_seed=2100):
+        gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+        strat = random_profile(gp, rng)
+        r = o2.valuate(gp, strat)
+        top = play_tops(gp, strat, r["cls"])
+        fin = [v for v in range(gp["n"]) if r["cls"][v] == o2.FIN]
+        pri = gp["pri"]
+        for u in fin:
+            assert np.sign(r["rank"][u] - r["sink_rank"]) == (1 if pri[top[u]] % 2 == 0 else -1)
+        for _ in range(400):
+            if len(fin) < 2:
+                break
+            u, w = (int(x) for x in rng.choice(fin, 2, replace=False))
+            if top[u] == top[w]:
+                continue
+            t = top[u] if pri[top[u]] > pri[top[w]] else top[w]
+            expect = 1 if (t == top[u]) == (pri[t] % 2 == 0) else -1
+            assert np.sign(r["rank"][u] - r["rank"][w]) == expect
+            checked += 1
+    assert checked > 1000
+
+
+def test_odd_choice_follows_top_words_unless_best_tops_tie():
+    # An Odd vertex's choice (the first minimiser of its successors' valuations, TOP above every finite one) is
+    # fixed by the successors' tops alone unless two finite successors share the best top so far: the Odd
+    # switching pass skips a vertex none of whose successors' top words changed, unless such a tie kept its mark.
+    rng = np.random.default_rng(22)
+    decided = 0
+    for s, g in small_games(40, 30, 600, 2, 5, base_seed=2200):
+        gp = o2.preprocess(g.n, g.offsets, g.targets, g.owner, g.pri)
+        strat = random_profile(gp, rng)
+        r = o2.valuate(gp, strat)
+        top = play_tops(gp, strat, r["cls"])
+        pri = gp["pri"]
+        for v in range(gp["n"]):
+            if gp["own"][v] != 1:
+                continue
+            succ = [int(gp["tgt"][e]) for e in range(gp["off"][v], gp["off"][v + 1])]
+            if any(r["cls"][t] == o2.ODDCYCLE for t in succ):
+                continue
+            want = succ[0]
+            for t in succ[1:]:
+                if r["rank"][t] < r["rank"][want]:
+                    want = t
+            best, tie = succ[0], False
+            for t in succ[1:]:
+                tt, tb = r["cls"][t] == o2.TOP, r["cls"][best] == o2.TOP
+                if tt or tb:
+                    less = tb and not tt  # a finite valuation is below TOP; TOP equals TOP
+                elif top[t] == top[best]:
+                    tie = True  # a chain comparison
+                    break
+                else:
+                    hi = top[t] if pri[top[t]] > pri[top[best]] else top[best]
+                    less = (hi == top[t]) == (pri[hi] % 2 == 1)  # t below best for Even
+                if less:
+                    best = t
+            if not tie:
+                assert best == want, (s, v)
+                decided += 1
+    assert decided > 300
+
+
 def test_long_chain_profile_ranks():
     # one n-long successor chain: the hardest case for list ranking
     g, sigma = gen.chain_profile(3000, seed=4)
